@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: exact SCAN on a resident R-MAT scale-22 graph, one GB300.
+
+Workload (one "step"): the 21-query sweep eps in {1/5, 3/10, 2/5, 1/2, 3/5,
+7/10, 4/5} x mu in {2, 5, 10} over the R-MAT scale-22 / edge-factor-16 graph
+(a=.57, b=.19, c=.19, seed 2; 4,194,304 vertices, 64,154,111 undirected
+edges), each query a full recompute (common counts, eps-test, cores,
+clusters, borders, hub/outlier). Metric: undirected edges clustered per
+second. Inputs (513 MB adjacency) are larger than L2, so no L2 flush is used.
+
+  value    device-resident: graph loaded, outputs written to device buffers
+  e2e      through the C ABI with host buffers: upload from pinned host memory,
+           load-time preparation, 21 host-result queries, free -- every step
+  roofline the similarity kernel: algorithmic bytes / CUDA-event duration
+  cpu_baseline  the CPU oracle (as it stands) on a bounded sample
+
+--impl reference times the CPU oracle on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "SCAN edges/s"
+UNIT = "edges/s"
+WORKLOAD = "rmat_s22_ef16_sweep21"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["recompute", "plain", "cache"], default="recompute")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain GPU path comparator")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
+    return ap.parse_args()
+
+
+def sweep():
+    return [(p, q, mu) for (p, q) in gg.EPS_SWEEP for mu in gg.MU_SWEEP]
+
+
+def make_graph(scale: int):
+    if scale == 22:
+        return gg.rmat_s22()
+    return gg.rmat(scale, 16, seed=2)
+
+
+def oriented_dmin(g):
+    """(dmin+1, dmax+1) closed sizes of every degree-oriented edge."""
+    deg = g.degrees()
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dst = g.adj.astype(np.int64)
+    ds, dd = deg[src], deg[dst]
+    fwd = (dd > ds) | ((dd == ds) & (dst > src))
+    return ds[fwd] + 1, dd[fwd] + 1
+
+
+def algorithmic_bytes(g, dmin1, dmax1, p, q):
+    """Bytes the similarity stage must move for one query: the smaller row of
+    every edge the degrees do not decide (4 B per id), every row once as the
+    larger side, one similarity byte per slot, and the offsets."""
+    dmin1 = dmin1.astype(np.float64)
+    dmax1 = dmax1.astype(np.float64)
+    pruned_dis = dmin1 * q * q < p * p * dmax1
+    pruned_sim = 4 * q * q >= p * p * dmin1 * dmax1
+    live = ~pruned_dis & ~pruned_sim
+    return 4.0 * float((dmin1[live] - 1).sum()) + 4.0 * g.nnz + 1.0 * g.nnz + 8.0 * (g.n + 1)
+
+
+def full_count_bytes(g, dmin1):
+    return 4.0 * float((dmin1 - 1).sum()) + 4.0 * g.nnz + 4.0 * g.nnz + 8.0 * (g.n + 1)
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- cpu oracle
+def oracle_rate(g, seconds: float, seed: int = 0, threads: int | None = None):
+    """Oracle common-count step on a uniform sample of degree-oriented edges,
+    grown until it takes about `seconds`. Returns (edges/s, sample size, s)."""
+    import oracle
+
+    threads = threads or os.cpu_count()
+    deg = g.degrees()
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dst = g.adj.astype(np.int64)
+    fwd = np.flatnonzero((deg[dst] > deg[src]) | ((deg[dst] == deg[src]) & (dst > src)))
+    rng = np.random.default_rng(seed)
+    k = 2000
+    while True:
+        slots = rng.choice(fwd, size=min(k, len(fwd)), replace=False)
+        t = time.perf_counter()
+        oracle.counts_for_slots(g, slots, threads=threads)
+        el = time.perf_counter() - t
+        if el >= seconds * 0.5 or k >= len(fwd):
+            return len(slots) / el, len(slots), el, threads
+        k = int(min(len(fwd), k * max(2.0, seconds / max(el, 1e-3))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g = make_graph(args.scale)
+    vals = []
+    per_step = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    info = None
+    for i in range(args.warmup + args.steps):
+        rate, k, el, thr = oracle_rate(g, per_step, seed=i)
+        if i >= args.warmup:
+            vals.append(rate)
+            info = (k, el, thr)
+    value = statistics.median(vals)
+    sample = (f"oracle common-count step on {info[0]} uniformly sampled degree-oriented edges of the "
+              f"{WORKLOAD} graph per step ({info[1]:.1f} s); linear steps excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "i32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "m": g.m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info[2], "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2311_12281_gb300 as ps
+    from paper_2311_12281_gb300 import _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    _build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    g = make_graph(args.scale)
+    dmin1, dmax1 = oriented_dmin(g)
+    queries = sweep()
+    mode = {"recompute": ps.SCAN_Q_RECOMPUTE, "plain": ps.SCAN_Q_PLAIN, "cache": ps.SCAN_Q_AUTO}[args.mode]
+
+    ctx = ps.Context(local, stream=stream.cuda_stream)
+    dg = ctx.load(g)
+    if args.mode == "cache":
+        dg.query(1, 2, 2, ps.SCAN_Q_BUILD_CACHE)
+    n = g.n
+    core = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cid = torch.empty(n, dtype=torch.int32, device="cuda")
+    label = torch.empty(n, dtype=torch.uint8, device="cuda")
+    pairs = torch.empty(2 * g.nnz, dtype=torch.int32, device="cuda")
+    npairs = torch.empty(1, dtype=torch.int64, device="cuda")
+
+    def step(qmode):
+        for (p, q, mu) in queries:
+            ps.scan_query_device(dg.handle, p, q, mu, qmode, core.data_ptr(), cid.data_ptr(), label.data_ptr(),
+                                 pairs.data_ptr(), g.nnz, npairs.data_ptr())
+
+    for _ in range(args.warmup):
+        step(mode)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ps.scan_ctx_profile(ctx.handle, True)
+    launches0 = ctx.kernel_launches
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(mode)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = t0.elapsed_time(t1)
+    launches = ctx.kernel_launches - launches0
+    stage_ms = {ps.STAGE_NAMES[s]: ps.scan_ctx_stage_time(ctx.handle, s) for s in range(5)}
+    ps.scan_ctx_profile(ctx.handle, False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    edges_per_step = len(queries) * g.m
+    value = world * edges_per_step / (ms_per_step / 1e3)
+
+    # roofline of the similarity stage (the dominant kernel)
+    sim_ms, sim_n = stage_ms["similarity"]
+    if args.mode == "recompute":
+        b_step = sum(algorithmic_bytes(g, dmin1, dmax1, p, q) for (p, q, mu) in queries)
+    else:
+        b_step = full_count_bytes(g, dmin1) * (len(queries) if args.mode == "plain" else 0)
+    achieved = (b_step * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        from paper_2311_12281_gb300._build import kernel_hash
+        if tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == WORKLOAD and tr.get("mode") == args.mode:
+            traffic = tr.get("bytes_per_launch")
+    except (OSError, ImportError, ValueError):
+        pass
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), seed 2",
+                   "n": g.n, "m": g.m, "queries_per_step": len(queries), "mode": args.mode,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (adjacency 513 MB), no flush"},
+        "roofline": {"bound": "hbm", "kernel": "similarity stage", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "bytes_per_step": b_step, "launches": sim_n,
+                     "avg_ms": sim_ms / max(sim_n, 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage_ms.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # plain GPU path comparator: one sweep step
+    if not args.no_plain and args.mode == "recompute" and rank == 0:
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(ps.SCAN_Q_PLAIN)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        result["plain_gpu"] = {"value": edges_per_step / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                               "what": "binary-search intersection of every edge, no pruning, no cache"}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        off_pin = torch.from_numpy(g.offsets).pin_memory()
+        adj_pin = torch.from_numpy(g.adj).pin_memory()
+        h2d = off_pin.numel() * 8 + adj_pin.numel() * 4
+
+        def e2e_step():
+            h = ps.scan_graph_load(ctx.handle, g.n, off_pin.numpy(), adj_pin.numpy())
+            d2h = 0
+            for (p, q, mu) in queries:
+                r = ps.scan_query_ex(h, p, q, mu, mode if args.mode != "cache" else ps.SCAN_Q_BUILD_CACHE)
+                d2h += r["core"].nbytes + r["cid"].nbytes + r["label"].nbytes + r["pairs"].nbytes + 8
+            ps.scan_graph_free(h)
+            return d2h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = time.perf_counter()
+        ke = max(1, min(args.steps, 2))
+        d2h = 0
+        for _ in range(ke):
+            d2h = e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t) / ke
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        result["e2e"] = {"value": world * edges_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h, "s_per_step": e2e_s}
+
+    dg.free()
+    ctx.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, k, el, thr = oracle_rate(g, 15.0)
+        result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                  "sample": f"oracle common-count step on {k} uniformly sampled degree-oriented "
+                                            f"edges ({el:.1f} s); linear steps excluded"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

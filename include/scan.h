@@ -1,0 +1,195 @@
+/*
+ * scan.h -- C ABI of libscan.so: exact structural graph clustering (SCAN)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (GPUSCAN++, Section 2.1, Definitions 2.1-2.3, Core,
+ * Structural Reachability, Cluster, Hub and Outlier): for an undirected
+ * simple graph and eps = eps_num/eps_den, mu, compute
+ *   sigma(u,v) = |N[u] cap N[v]| / sqrt(|N[u]| |N[v]|) over closed
+ *   neighbourhoods for every edge, the eps-test (exact: cn^2 q^2 >= p^2
+ *   |N[u]| |N[v]| in 128-bit integers), the cores (|N_eps[u]| >= mu), the
+ *   clusters (connected components of cores through eps-similar core-core
+ *   edges; each cluster is named by its smallest core id), every
+ *   (vertex, cluster) membership of non-core vertices, and the hub/outlier
+ *   label of every vertex in no cluster (hub iff its neighbours' memberships
+ *   span >= 2 clusters).
+ *
+ * Conventions for every call:
+ *   - Return value: scan_status (SCAN_OK = 0). On failure nothing is
+ *     returned through out-parameters and scan_last_error() (thread-local)
+ *     describes the failure. No call aborts, exits or throws across the ABI.
+ *   - Vertex ids are int32 in [0, n); CSR offsets are int64[n + 1].
+ *   - Host pointers stay owned by the caller unless stated otherwise.
+ *   - Objects (ctx, graph, result, server) are owned by the library and
+ *     released with their *_free / *_destroy call. A graph must be freed
+ *     before its context is destroyed.
+ *   - A context is not thread-safe: calls on one context (and its graphs)
+ *     must be serialised by the caller. Distinct contexts are independent.
+ */
+#ifndef SCAN_H
+#define SCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SCAN_API __attribute__((visibility("default")))
+#else
+#define SCAN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum scan_status {
+    SCAN_OK = 0,
+    SCAN_EINVAL = 1,   /* bad argument or malformed graph (detail names the first bad index) */
+    SCAN_ENOMEM = 2,   /* a host or device allocation failed */
+    SCAN_EBUDGET = 3,  /* the request does not fit the context's device-memory budget */
+    SCAN_ECUDA = 4,    /* a CUDA runtime error (detail has the CUDA error string) */
+    SCAN_ETIMEOUT = 5, /* a bounded device loop ran out of iterations (kernel returned early) */
+    SCAN_EBUSY = 6     /* a server request can never be admitted, or the server is shutting down */
+} scan_status;
+
+/* Vertex labels of a result. */
+enum { SCAN_CORE = 0, SCAN_BORDER = 1, SCAN_HUB = 2, SCAN_OUTLIER = 3 };
+
+typedef struct scan_ctx scan_ctx;
+typedef struct scan_graph scan_graph;
+typedef struct scan_result scan_result;
+
+/* Thread-local description of the last failure on this thread ("" if none).
+ * The pointer stays valid until the next failing call on this thread. */
+SCAN_API const char *scan_last_error(void);
+
+/* ------------------------------------------------------------- context */
+typedef struct scan_ctx_opts {
+    int32_t device;        /* CUDA device ordinal */
+    uint64_t budget_bytes; /* cap on device memory this context may hold; 0 = no cap */
+    void *stream;          /* cudaStream_t to launch on; NULL = a stream the context creates */
+} scan_ctx_opts;
+
+/* Create a context on opts->device (opts may be NULL: device 0, no cap, own
+ * stream). Errors: SCAN_EINVAL (bad device), SCAN_ECUDA, SCAN_ENOMEM. */
+SCAN_API scan_status scan_ctx_create(const scan_ctx_opts *opts, scan_ctx **out);
+SCAN_API void scan_ctx_destroy(scan_ctx *ctx);
+/* Device bytes the context currently holds (graphs, caches, scratch). */
+SCAN_API uint64_t scan_ctx_device_bytes(const scan_ctx *ctx);
+/* Number of CUDA kernels this context has launched so far. */
+SCAN_API uint64_t scan_ctx_kernel_launches(const scan_ctx *ctx);
+/* Synchronise the context's stream. */
+SCAN_API scan_status scan_ctx_sync(scan_ctx *ctx);
+
+/* Per-stage device timing with CUDA events recorded on the context's stream
+ * around each stage of every query (the paper reports per-phase times in its
+ * Table 3; these are the same phases, split finer). */
+enum {
+    SCAN_STAGE_SIMILARITY = 0, /* common counts + eps-test (Algorithm 2's checkSim work) */
+    SCAN_STAGE_CORE = 1,       /* |N_eps| >= mu */
+    SCAN_STAGE_CLUSTER = 2,    /* union-find over core-core similar edges */
+    SCAN_STAGE_BORDER = 3,     /* border memberships */
+    SCAN_STAGE_LABEL = 4,      /* hub / outlier */
+    SCAN_STAGE_COUNT = 5
+};
+/* enable != 0 turns recording on and clears the totals; 0 turns it off. */
+SCAN_API scan_status scan_ctx_profile(scan_ctx *ctx, int32_t enable);
+/* Synchronises, then returns the summed milliseconds and number of timed
+ * intervals of a stage since profiling was (re)enabled. */
+SCAN_API scan_status scan_ctx_stage_time(scan_ctx *ctx, int32_t stage, double *total_ms, int64_t *intervals);
+
+/* ---------------------------------------------------------------- graph */
+/* Load flags. */
+#define SCAN_LOAD_DEVICE_PTRS 0x1u   /* offsets/adj are device pointers (copied device-to-device) */
+#define SCAN_LOAD_PINNED_BORROW 0x2u /* partitioned mode: keep the CSR in the caller's host memory
+                                        (registered as pinned; the caller keeps it alive and
+                                        unmodified until scan_graph_free) and stream slices */
+
+/*
+ * Load an undirected simple graph given as CSR: offsets int64[n + 1] with
+ * offsets[0] = 0 and offsets[n] = nnz, adj int32[nnz] (nnz = 2m directed
+ * slots). The CSR layout is the vertex array / adjacency array of the
+ * paper's CSR-enhanced layout (Section 4.1).
+ *
+ * Requirements (checked on the device; nothing is repaired): each row sorted
+ * strictly ascending (so no duplicates), ids in [0, n), no self-loops, and
+ * symmetric (v in row u <=> u in row v). Violations: SCAN_EINVAL with the
+ * first bad slot in scan_last_error(). n = 0 is valid.
+ *
+ * Without SCAN_LOAD_PINNED_BORROW the library copies the arrays to the
+ * device and the caller may release them on return. If the graph's device
+ * footprint exceeds the budget: SCAN_EBUDGET (pass SCAN_LOAD_PINNED_BORROW
+ * to cluster it out of core). With SCAN_LOAD_PINNED_BORROW the host arrays
+ * must stay valid until scan_graph_free.
+ */
+SCAN_API scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj,
+                            int64_t nnz, uint32_t flags, scan_graph **out);
+SCAN_API void scan_graph_free(scan_graph *g);
+SCAN_API int32_t scan_graph_n(const scan_graph *g);
+SCAN_API int64_t scan_graph_nnz(const scan_graph *g);
+/* Device bytes held by this graph (including its count cache). */
+SCAN_API uint64_t scan_graph_device_bytes(const scan_graph *g);
+/* Release the per-edge common-count cache, if any. */
+SCAN_API scan_status scan_graph_drop_cache(scan_graph *g);
+/* 1 if the graph holds a valid per-edge common-count cache. */
+SCAN_API int32_t scan_graph_has_cache(const scan_graph *g);
+/* Copy the cached closed common counts |N[u] cap N[v]| (the numerator of
+ * Definition 2.2's sigma, Eq. 1) to host memory out[nnz], slot-aligned with
+ * adj. Requires a cache (a query with SCAN_Q_BUILD_CACHE), else SCAN_EINVAL.
+ * Synchronous. */
+SCAN_API scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out);
+
+/* --------------------------------------------------------------- query */
+typedef struct scan_params {
+    uint32_t eps_num; /* eps = eps_num / eps_den, 0 < eps <= 1 (Definition 2.3) */
+    uint32_t eps_den;
+    uint32_t mu;      /* mu >= 2 (Definition Core) */
+} scan_params;
+
+/* Query modes. */
+#define SCAN_Q_AUTO 0x0u        /* use the count cache if present, else full recompute */
+#define SCAN_Q_RECOMPUTE 0x1u   /* full recompute with degree pruning; ignore any cache */
+#define SCAN_Q_PLAIN 0x2u       /* comparator path: per-edge binary-search intersection of every
+                                   edge, no pruning, no cache (Algorithm 2's checkSim, exact) */
+#define SCAN_Q_BUILD_CACHE 0x4u /* compute every edge's common count, keep it on the graph,
+                                   then answer from it */
+
+/*
+ * One SCAN query. Requires 0 < eps_num <= eps_den and mu >= 2, else
+ * SCAN_EINVAL. The result lives in library-owned host memory until
+ * scan_result_free. Synchronous: returns when the result is on the host.
+ */
+SCAN_API scan_status scan_query(scan_graph *g, uint32_t eps_num, uint32_t eps_den, uint32_t mu, scan_result **out);
+SCAN_API scan_status scan_query_ex(scan_graph *g, const scan_params *params, uint32_t mode, scan_result **out);
+
+SCAN_API int32_t scan_result_n(const scan_result *r);
+SCAN_API const uint8_t *scan_result_core(const scan_result *r);     /* [n] 1 = core */
+SCAN_API const int32_t *scan_result_cluster(const scan_result *r);  /* [n] cluster id for cores, -1 otherwise */
+SCAN_API const uint8_t *scan_result_label(const scan_result *r);    /* [n] SCAN_CORE/BORDER/HUB/OUTLIER */
+SCAN_API int64_t scan_result_border_count(const scan_result *r);    /* k */
+SCAN_API const int32_t *scan_result_border_pairs(const scan_result *r); /* [2k] (v, c) ascending by (v, c) */
+SCAN_API void scan_result_free(scan_result *r);
+
+/*
+ * Device-resident query: writes into caller-provided device buffers on the
+ * context's stream and does not synchronise. Buffers: core uint8[n],
+ * cid int32[n], label uint8[n], pairs int32[2 * pairs_cap], npairs int64[1]
+ * (device). pairs_cap >= nnz always suffices (a non-core has fewer than mu-1
+ * similar neighbours, so k <= nnz). If k > pairs_cap only the first
+ * pairs_cap pairs are written and *npairs still holds k.
+ */
+typedef struct scan_device_out {
+    uint8_t *core;
+    int32_t *cid;
+    uint8_t *label;
+    int32_t *pairs;
+    int64_t pairs_cap;
+    int64_t *npairs;
+} scan_device_out;
+
+SCAN_API scan_status scan_query_device(scan_graph *g, const scan_params *params, uint32_t mode, const scan_device_out *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCAN_H */

@@ -53,6 +53,8 @@ def _lib():
         lib.oracle_common_counts.argtypes = [i64, vp, vp, vp, i32]
         lib.oracle_scan.restype = i32
         lib.oracle_scan.argtypes = [i64, vp, vp, u32, u32, u32, i32, vp, vp, vp, vp, vp, vp]
+        lib.oracle_counts_for_slots.restype = None
+        lib.oracle_counts_for_slots.argtypes = [i64, vp, vp, vp, i64, vp, i32]
         lib.brute_scan.restype = i32
         lib.brute_scan.argtypes = [i32, vp, u32, u32, u32, vp, vp, vp, vp, vp]
         lib.brute_exhaustive.restype = i64
@@ -86,6 +88,17 @@ def common_counts(graph, threads: int = 0) -> np.ndarray:
     cn = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
     _lib().oracle_common_counts(graph.n, off.ctypes.data, adj.ctypes.data, cn.ctypes.data, int(threads))
     return cn[: int(off[-1])]
+
+
+def counts_for_slots(graph, slots, threads: int = 0) -> np.ndarray:
+    """|N[u] & N[v]| for the given slots only, each computed independently."""
+    off, adj = _csr(graph)
+    sl = np.ascontiguousarray(slots, dtype=np.int64)
+    out = np.zeros(max(len(sl), 1), dtype=np.int32)
+    if len(sl):
+        _lib().oracle_counts_for_slots(graph.n, off.ctypes.data, adj.ctypes.data, sl.ctypes.data, len(sl),
+                                       out.ctypes.data, int(threads))
+    return out[: len(sl)]
 
 
 def scan(graph, eps_num: int, eps_den: int, mu: int, threads: int = 0, want_cn: bool = False) -> dict:

@@ -288,3 +288,32 @@ int oracle_scan(int64_t n, const int64_t *off, const int32_t *adj, uint32_t p, u
     free(sim); free(queue); free(boff); free(scratch);
     return ORACLE_OK;
 }
+
+/*
+ * Definition 2.2 numerator for selected slots only (sampled full-size
+ * checks): out[i] = |N[u] cap N[v]| for the slot slots[i] = (u, v), where u
+ * is the row holding the slot. Each count is computed independently.
+ */
+void oracle_counts_for_slots(int64_t n, const int64_t *off, const int32_t *adj, const int64_t *slots, int64_t k,
+                             int32_t *out, int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < k; ++i) {
+        int64_t s = slots[i], lo = 0, hi = n;
+        while (hi - lo > 1) { /* row u with off[u] <= s < off[u+1] */
+            int64_t mid = lo + (hi - lo) / 2;
+            if (off[mid] <= s) lo = mid; else hi = mid;
+        }
+        while (lo + 1 <= n && off[lo + 1] <= s) ++lo; /* skip empty rows sharing the offset */
+        int64_t u = lo, v = adj[s];
+        int64_t du = off[u + 1] - off[u], dv = off[v + 1] - off[v];
+        int64_t big = du > dv ? du : dv, small = du > dv ? dv : du;
+        int64_t c = (small == 0 || big / small <= 32) ? count_merge(adj + off[u], du, adj + off[v], dv)
+                                                       : count_search(adj + off[u], du, adj + off[v], dv);
+        out[i] = (int32_t)(c + 2);
+    }
+}

@@ -1,0 +1,302 @@
+"""Exact SCAN structural graph clustering on one GB300 -- Python binding.
+
+A thin ctypes binding of ``libscan.so`` (declared in ``include/scan.h``): the
+functions below carry the C names and only marshal arguments. Every step of a
+query runs in the library's CUDA kernels; there is no CPU fallback, and
+importing this package fails loudly if the library has not been built
+(``paper_2311_12281_gb300._build.build()``).
+
+Results compare field by field with the CPU oracle: ``core`` uint8[n],
+``cid`` int32[n] (smallest core id of the cluster, -1 for non-cores), ``label``
+uint8[n] (0 core, 1 border, 2 hub, 3 outlier), ``pairs`` int32[k, 2] of
+(vertex, cluster id) memberships of non-core vertices, ascending.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libscan.so")
+
+SCAN_OK, SCAN_EINVAL, SCAN_ENOMEM, SCAN_EBUDGET, SCAN_ECUDA, SCAN_ETIMEOUT, SCAN_EBUSY = range(7)
+SCAN_CORE, SCAN_BORDER, SCAN_HUB, SCAN_OUTLIER = range(4)
+SCAN_LOAD_DEVICE_PTRS = 0x1
+SCAN_LOAD_PINNED_BORROW = 0x2
+SCAN_Q_AUTO, SCAN_Q_RECOMPUTE, SCAN_Q_PLAIN, SCAN_Q_BUILD_CACHE = 0x0, 0x1, 0x2, 0x4
+
+_STATUS = {1: "SCAN_EINVAL", 2: "SCAN_ENOMEM", 3: "SCAN_EBUDGET", 4: "SCAN_ECUDA", 5: "SCAN_ETIMEOUT",
+           6: "SCAN_EBUSY"}
+
+
+class ScanError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class scan_ctx_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class scan_params(ctypes.Structure):
+    _fields_ = [("eps_num", ctypes.c_uint32), ("eps_den", ctypes.c_uint32), ("mu", ctypes.c_uint32)]
+
+
+class scan_device_out(ctypes.Structure):
+    _fields_ = [("core", ctypes.c_void_p), ("cid", ctypes.c_void_p), ("label", ctypes.c_void_p),
+                ("pairs", ctypes.c_void_p), ("pairs_cap", ctypes.c_int64), ("npairs", ctypes.c_void_p)]
+
+
+# C signatures: name -> (restype, argtypes)
+_VP, _I32, _U32, _I64, _U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+_PP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "scan_last_error": (ctypes.c_char_p, []),
+    "scan_ctx_create": (ctypes.c_int, [ctypes.POINTER(scan_ctx_opts), _PP]),
+    "scan_ctx_destroy": (None, [_VP]),
+    "scan_ctx_device_bytes": (_U64, [_VP]),
+    "scan_ctx_kernel_launches": (_U64, [_VP]),
+    "scan_ctx_sync": (ctypes.c_int, [_VP]),
+    "scan_ctx_profile": (ctypes.c_int, [_VP, _I32]),
+    "scan_ctx_stage_time": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "scan_graph_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _U32, _PP]),
+    "scan_graph_free": (None, [_VP]),
+    "scan_graph_n": (_I32, [_VP]),
+    "scan_graph_nnz": (_I64, [_VP]),
+    "scan_graph_device_bytes": (_U64, [_VP]),
+    "scan_graph_drop_cache": (ctypes.c_int, [_VP]),
+    "scan_graph_has_cache": (_I32, [_VP]),
+    "scan_graph_copy_counts": (ctypes.c_int, [_VP, _VP]),
+    "scan_query": (ctypes.c_int, [_VP, _U32, _U32, _U32, _PP]),
+    "scan_query_ex": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, _PP]),
+    "scan_query_device": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, ctypes.POINTER(scan_device_out)]),
+    "scan_result_n": (_I32, [_VP]),
+    "scan_result_core": (_VP, [_VP]),
+    "scan_result_cluster": (_VP, [_VP]),
+    "scan_result_label": (_VP, [_VP]),
+    "scan_result_border_count": (_I64, [_VP]),
+    "scan_result_border_pairs": (_VP, [_VP]),
+    "scan_result_free": (None, [_VP]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libscan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libscan.so not built at {LIB_PATH}; run paper_2311_12281_gb300._build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int):
+    if status != SCAN_OK:
+        raise ScanError(status, (lib().scan_last_error() or b"").decode())
+
+
+# ----------------------------------------------------------- same-name calls
+def scan_last_error() -> str:
+    return (lib().scan_last_error() or b"").decode()
+
+
+def scan_ctx_create(device: int = 0, budget_bytes: int = 0, stream: int | None = None) -> int:
+    opts = scan_ctx_opts(device, budget_bytes, stream or None)
+    out = ctypes.c_void_p()
+    _check(lib().scan_ctx_create(ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def scan_ctx_destroy(ctx: int):
+    lib().scan_ctx_destroy(ctx)
+
+
+def scan_ctx_device_bytes(ctx: int) -> int:
+    return int(lib().scan_ctx_device_bytes(ctx))
+
+
+def scan_ctx_kernel_launches(ctx: int) -> int:
+    return int(lib().scan_ctx_kernel_launches(ctx))
+
+
+def scan_ctx_sync(ctx: int):
+    _check(lib().scan_ctx_sync(ctx))
+
+
+SCAN_STAGE_SIMILARITY, SCAN_STAGE_CORE, SCAN_STAGE_CLUSTER, SCAN_STAGE_BORDER, SCAN_STAGE_LABEL = range(5)
+STAGE_NAMES = ("similarity", "core", "cluster", "border", "label")
+
+
+def scan_ctx_profile(ctx: int, enable: bool):
+    _check(lib().scan_ctx_profile(ctx, 1 if enable else 0))
+
+
+def scan_ctx_stage_time(ctx: int, stage: int) -> tuple[float, int]:
+    """(summed milliseconds, number of timed intervals) of one stage."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(lib().scan_ctx_stage_time(ctx, stage, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def scan_graph_load(ctx: int, n: int, offsets, adj, nnz: int | None = None, flags: int = 0) -> int:
+    """offsets/adj: numpy arrays (host) or integer device addresses with
+    flags |= SCAN_LOAD_DEVICE_PTRS."""
+    out = ctypes.c_void_p()
+    if flags & SCAN_LOAD_DEVICE_PTRS:
+        po, pa = int(offsets), int(adj)
+        assert nnz is not None
+    else:
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        adj = np.ascontiguousarray(adj, dtype=np.int32)
+        nnz = int(adj.size) if nnz is None else nnz
+        po = offsets.ctypes.data if offsets.size else None
+        pa = adj.ctypes.data if adj.size else None
+    _check(lib().scan_graph_load(ctx, int(n), po, pa, int(nnz), int(flags), ctypes.byref(out)))
+    return out.value
+
+
+def scan_graph_free(g: int):
+    lib().scan_graph_free(g)
+
+
+def scan_graph_n(g: int) -> int:
+    return int(lib().scan_graph_n(g))
+
+
+def scan_graph_nnz(g: int) -> int:
+    return int(lib().scan_graph_nnz(g))
+
+
+def scan_graph_device_bytes(g: int) -> int:
+    return int(lib().scan_graph_device_bytes(g))
+
+
+def scan_graph_drop_cache(g: int):
+    _check(lib().scan_graph_drop_cache(g))
+
+
+def scan_graph_has_cache(g: int) -> bool:
+    return bool(lib().scan_graph_has_cache(g))
+
+
+def scan_graph_copy_counts(g: int, nnz: int) -> np.ndarray:
+    """Per-slot closed common counts from the graph's cache (int32[nnz])."""
+    out = np.zeros(max(nnz, 1), dtype=np.int32)
+    _check(lib().scan_graph_copy_counts(g, out.ctypes.data))
+    return out[:nnz]
+
+
+def _result_to_numpy(r: int) -> dict:
+    L = lib()
+    n = L.scan_result_n(r)
+    k = L.scan_result_border_count(r)
+
+    def arr(ptr, dtype, count):
+        if count == 0:
+            return np.zeros(0, dtype=dtype)
+        buf = (ctypes.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
+        return np.frombuffer(buf, dtype=dtype, count=count).copy()
+
+    out = {
+        "core": arr(L.scan_result_core(r), np.uint8, n),
+        "cid": arr(L.scan_result_cluster(r), np.int32, n),
+        "label": arr(L.scan_result_label(r), np.uint8, n),
+        "pairs": arr(L.scan_result_border_pairs(r), np.int32, 2 * k).reshape(k, 2),
+    }
+    L.scan_result_free(r)
+    return out
+
+
+def scan_query(g: int, eps_num: int, eps_den: int, mu: int) -> dict:
+    out = ctypes.c_void_p()
+    _check(lib().scan_query(g, eps_num, eps_den, mu, ctypes.byref(out)))
+    return _result_to_numpy(out.value)
+
+
+def scan_query_ex(g: int, eps_num: int, eps_den: int, mu: int, mode: int = SCAN_Q_AUTO) -> dict:
+    out = ctypes.c_void_p()
+    p = scan_params(eps_num, eps_den, mu)
+    _check(lib().scan_query_ex(g, ctypes.byref(p), mode, ctypes.byref(out)))
+    return _result_to_numpy(out.value)
+
+
+def scan_query_device(g: int, eps_num: int, eps_den: int, mu: int, mode: int, core: int, cid: int, label: int,
+                      pairs: int, pairs_cap: int, npairs: int):
+    """Device-resident query into caller-owned device buffers (addresses)."""
+    p = scan_params(eps_num, eps_den, mu)
+    o = scan_device_out(core, cid, label, pairs, pairs_cap, npairs)
+    _check(lib().scan_query_device(g, ctypes.byref(p), mode, ctypes.byref(o)))
+
+
+# --------------------------------------------------------------- convenience
+class Context:
+    """Owns a scan_ctx; graphs loaded through it are freed with it."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, stream: int | None = None):
+        self.handle = scan_ctx_create(device, budget_bytes, stream)
+        self._graphs = []
+
+    def load(self, graph, flags: int = 0) -> "Graph":
+        g = Graph(self, scan_graph_load(self.handle, graph.n, graph.offsets, graph.adj, None, flags), graph.n)
+        self._graphs.append(g)
+        return g
+
+    @property
+    def kernel_launches(self) -> int:
+        return scan_ctx_kernel_launches(self.handle)
+
+    @property
+    def device_bytes(self) -> int:
+        return scan_ctx_device_bytes(self.handle)
+
+    def sync(self):
+        scan_ctx_sync(self.handle)
+
+    def close(self):
+        for g in self._graphs:
+            g.free()
+        self._graphs = []
+        if self.handle:
+            scan_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Graph:
+    def __init__(self, ctx: Context, handle: int, n: int):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def query(self, eps_num: int, eps_den: int, mu: int, mode: int = SCAN_Q_AUTO) -> dict:
+        return scan_query_ex(self.handle, eps_num, eps_den, mu, mode)
+
+    def drop_cache(self):
+        scan_graph_drop_cache(self.handle)
+
+    def counts(self) -> np.ndarray:
+        return scan_graph_copy_counts(self.handle, int(lib().scan_graph_nnz(self.handle)))
+
+    @property
+    def has_cache(self) -> bool:
+        return scan_graph_has_cache(self.handle)
+
+    def free(self):
+        if self.handle:
+            scan_graph_free(self.handle)
+            self.handle = None

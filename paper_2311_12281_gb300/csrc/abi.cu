@@ -1,0 +1,392 @@
+// abi.cu -- the C ABI of libscan.so (declared in include/scan.h).
+//
+// Every entry point catches C++ exceptions and CUDA errors and maps them to
+// a scan_status; the detail goes to a thread-local message.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "scan_internal.cuh"
+
+namespace scan {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+scan_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+    return SCAN_ECUDA;
+}
+
+scan_status dev_alloc(Ctx *c, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->budget && c->used + bytes > c->budget) {
+        set_error("device budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
+                  std::to_string(c->used) + " of " + std::to_string(c->budget) + " in use");
+        return SCAN_EBUDGET;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        return SCAN_ENOMEM;
+    }
+    b.ptr = p;
+    b.bytes = bytes;
+    c->used += bytes;
+    return SCAN_OK;
+}
+
+void dev_free(Ctx *c, DevBuf &b) {
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        c->used -= b.bytes;
+    }
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+static void graph_release(Graph *g) {
+    Ctx *c = g->ctx;
+    DevBuf *bufs[] = {&g->off, &g->adj, &g->src, &g->rev, &g->deg, &g->oe, &g->cn_cache, &g->sim,
+                      &g->core, &g->cid, &g->parent, &g->label, &g->cnt, &g->cnt_off, &g->ucnt,
+                      &g->pair_off, &g->raw, &g->pairs, &g->npairs, &g->scan_tmp, &g->err};
+    for (DevBuf *b : bufs) dev_free(c, *b);
+    if (g->h_npairs) cudaFreeHost(g->h_npairs);
+    if (g->h_err) cudaFreeHost(g->h_err);
+    g->h_npairs = nullptr;
+    g->h_err = nullptr;
+}
+
+static scan_status check_params(const scan_params *p) {
+    if (!p) { set_error("params is NULL"); return SCAN_EINVAL; }
+    if (p->eps_num == 0 || p->eps_den == 0 || p->eps_num > p->eps_den) {
+        set_error("eps must satisfy 0 < eps_num <= eps_den (0 < eps <= 1)");
+        return SCAN_EINVAL;
+    }
+    if (p->mu < 2) { set_error("mu must be >= 2"); return SCAN_EINVAL; }
+    return SCAN_OK;
+}
+
+// Reads and clears the graph's device error word after a synchronisation.
+static scan_status take_device_error(Graph *g) {
+    Ctx *c = g->ctx;
+    SCAN_CUDA(cudaMemcpyAsync(g->h_err, g->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));
+    if (*g->h_err) {
+        uint32_t e = *g->h_err;
+        SCAN_CUDA(cudaMemsetAsync(g->err.ptr, 0, sizeof(uint32_t), c->stream));
+        set_error("a bounded device loop gave up (error bits " + std::to_string(e) + ")");
+        return SCAN_ETIMEOUT;
+    }
+    return SCAN_OK;
+}
+
+}  // namespace scan
+
+using namespace scan;
+
+struct scan_ctx : Ctx {};
+struct scan_graph : Graph {};
+struct scan_result {
+    int32_t n = 0;
+    int64_t k = 0;
+    uint8_t *core = nullptr;
+    int32_t *cid = nullptr;
+    uint8_t *label = nullptr;
+    int32_t *pairs = nullptr;
+};
+
+#define ABI_GUARD_BEGIN try {
+#define ABI_GUARD_END                                   \
+    }                                                   \
+    catch (const std::bad_alloc &) {                    \
+        set_error("host allocation failed");            \
+        return SCAN_ENOMEM;                             \
+    }                                                   \
+    catch (...) {                                       \
+        set_error("internal error");                    \
+        return SCAN_EINVAL;                             \
+    }
+
+extern "C" {
+
+const char *scan_last_error(void) { return g_last_error.c_str(); }
+
+scan_status scan_ctx_create(const scan_ctx_opts *opts, scan_ctx **out) {
+    ABI_GUARD_BEGIN
+    if (!out) { set_error("out is NULL"); return SCAN_EINVAL; }
+    *out = nullptr;
+    int dev = opts ? opts->device : 0;
+    int count = 0;
+    SCAN_CUDA(cudaGetDeviceCount(&count));
+    if (dev < 0 || dev >= count) {
+        set_error("device ordinal " + std::to_string(dev) + " out of range (" + std::to_string(count) + " devices)");
+        return SCAN_EINVAL;
+    }
+    SCAN_CUDA(cudaSetDevice(dev));
+    scan_ctx *c = new scan_ctx();
+    c->device = dev;
+    c->budget = opts ? opts->budget_bytes : 0;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) {
+        if (opts && opts->stream) {
+            c->stream = (cudaStream_t)opts->stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "context setup");
+    }
+    *out = c;
+    return SCAN_OK;
+    ABI_GUARD_END
+}
+
+static void drop_marks(Ctx *c);
+
+void scan_ctx_destroy(scan_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    drop_marks(c);
+    if (c->own_stream && c->stream) {
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+uint64_t scan_ctx_device_bytes(const scan_ctx *c) { return c ? c->used : 0; }
+uint64_t scan_ctx_kernel_launches(const scan_ctx *c) { return c ? c->launches : 0; }
+
+scan_status scan_ctx_sync(scan_ctx *c) {
+    if (!c) { set_error("ctx is NULL"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(c->device));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));
+    return SCAN_OK;
+}
+
+static void drop_marks(Ctx *c) {
+    for (auto &m : c->marks) {
+        cudaEventDestroy(m.start);
+        cudaEventDestroy(m.stop);
+    }
+    c->marks.clear();
+}
+
+scan_status scan_ctx_profile(scan_ctx *c, int32_t enable) {
+    if (!c) { set_error("ctx is NULL"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(c->device));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));
+    drop_marks(c);
+    for (int s = 0; s < SCAN_STAGE_COUNT; ++s) { c->stage_ms[s] = 0; c->stage_n[s] = 0; }
+    c->profiling = enable != 0;
+    return SCAN_OK;
+}
+
+scan_status scan_ctx_stage_time(scan_ctx *c, int32_t stage, double *total_ms, int64_t *intervals) {
+    if (!c || !total_ms || stage < 0 || stage >= SCAN_STAGE_COUNT) { set_error("bad arguments"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(c->device));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto &m : c->marks) {
+        float ms = 0;
+        SCAN_CUDA(cudaEventElapsedTime(&ms, m.start, m.stop));
+        c->stage_ms[m.stage] += ms;
+        c->stage_n[m.stage] += 1;
+    }
+    drop_marks(c);
+    *total_ms = c->stage_ms[stage];
+    if (intervals) *intervals = c->stage_n[stage];
+    return SCAN_OK;
+}
+
+scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                            uint32_t flags, scan_graph **out) {
+    ABI_GUARD_BEGIN
+    if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj)) {
+        set_error("bad sizes or NULL arrays");
+        return SCAN_EINVAL;
+    }
+    if (nnz % 2 != 0) { set_error("nnz must be even for a symmetric graph"); return SCAN_EINVAL; }
+    if (n == 0 && nnz != 0) { set_error("an empty graph has nnz = 0"); return SCAN_EINVAL; }
+    if ((uint64_t)nnz >= (1ull << 32)) {
+        set_error("a resident graph needs nnz < 2^32 (use SCAN_LOAD_PINNED_BORROW)");
+        return SCAN_EINVAL;
+    }
+    if (flags & SCAN_LOAD_PINNED_BORROW) {
+        set_error("SCAN_LOAD_PINNED_BORROW is not available in this build");
+        return SCAN_EINVAL;
+    }
+    const bool on_dev = flags & SCAN_LOAD_DEVICE_PTRS;
+    if (!on_dev && n > 0) {  // cheap host-side check before any copy
+        if (offsets[0] != 0 || offsets[n] != nnz) {
+            set_error("offsets[0] must be 0 and offsets[n] must equal nnz");
+            return SCAN_EINVAL;
+        }
+    }
+    SCAN_CUDA(cudaSetDevice(ctx->device));
+    scan_graph *g = new scan_graph();
+    g->ctx = ctx;
+    g->n = n;
+    g->nnz = nnz;
+    g->m = nnz / 2;
+    auto fail = [&](scan_status s) {
+        graph_release(g);
+        delete g;
+        return s;
+    };
+    const size_t N1 = (size_t)n + 1, E = (size_t)(nnz > 0 ? nnz : 1), M = (size_t)(g->m > 0 ? g->m : 1);
+    struct { DevBuf *b; size_t bytes; } plan[] = {
+        {&g->off, 8 * N1}, {&g->adj, 4 * E}, {&g->src, 4 * E}, {&g->rev, 4 * E}, {&g->deg, 4 * N1},
+        {&g->oe, 4 * M}, {&g->sim, E}, {&g->core, N1}, {&g->cid, 4 * N1}, {&g->parent, 4 * N1},
+        {&g->label, N1}, {&g->cnt, 4 * N1}, {&g->cnt_off, 8 * N1}, {&g->ucnt, 4 * N1}, {&g->pair_off, 8 * N1},
+        {&g->raw, 4 * E}, {&g->pairs, 8 * E}, {&g->npairs, 8}, {&g->err, 4}};
+    for (auto &p : plan) {
+        scan_status s = dev_alloc(ctx, *p.b, p.bytes);
+        if (s != SCAN_OK) return fail(s);
+    }
+    cudaError_t e = cudaMallocHost(&g->h_npairs, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_err, sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "pinned staging"));
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = n > 0 ? cudaMemcpyAsync(g->off.ptr, offsets, 8 * N1, kind, ctx->stream)
+              : cudaMemsetAsync(g->off.ptr, 0, 8, ctx->stream);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(g->adj.ptr, adj, 4 * (size_t)nnz, kind, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->err.ptr, 0, 4, ctx->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "graph upload"));
+    scan_status s = graph_prepare(g);
+    if (s != SCAN_OK) return fail(s);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "graph prepare"));
+    *out = g;
+    return SCAN_OK;
+    ABI_GUARD_END
+}
+
+void scan_graph_free(scan_graph *g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    graph_release(g);
+    delete g;
+}
+
+int32_t scan_graph_n(const scan_graph *g) { return g ? g->n : 0; }
+int64_t scan_graph_nnz(const scan_graph *g) { return g ? g->nnz : 0; }
+
+uint64_t scan_graph_device_bytes(const scan_graph *g) {
+    if (!g) return 0;
+    const DevBuf *bufs[] = {&g->off, &g->adj, &g->src, &g->rev, &g->deg, &g->oe, &g->cn_cache, &g->sim,
+                            &g->core, &g->cid, &g->parent, &g->label, &g->cnt, &g->cnt_off, &g->ucnt,
+                            &g->pair_off, &g->raw, &g->pairs, &g->npairs, &g->scan_tmp, &g->err};
+    uint64_t s = 0;
+    for (const DevBuf *b : bufs) s += b->bytes;
+    return s;
+}
+
+scan_status scan_graph_drop_cache(scan_graph *g) {
+    if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(g->ctx->device));
+    SCAN_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    dev_free(g->ctx, g->cn_cache);
+    g->cache_valid = false;
+    return SCAN_OK;
+}
+
+int32_t scan_graph_has_cache(const scan_graph *g) { return g && g->cache_valid ? 1 : 0; }
+
+scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out) {
+    if (!g || !out) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
+    if (!g->cache_valid) { set_error("graph has no common-count cache"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(g->ctx->device));
+    if (g->nnz > 0)
+        SCAN_CUDA(cudaMemcpyAsync(out, g->cn_cache.ptr, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost,
+                                  g->ctx->stream));
+    SCAN_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    return SCAN_OK;
+}
+
+scan_status scan_query_device(scan_graph *g, const scan_params *params, uint32_t mode, const scan_device_out *o) {
+    ABI_GUARD_BEGIN
+    if (!g || !o) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
+    SCAN_TRY(check_params(params));
+    if (g->n > 0 && (!o->core || !o->cid || !o->label)) { set_error("NULL output array"); return SCAN_EINVAL; }
+    if (!o->npairs || (o->pairs_cap > 0 && !o->pairs) || o->pairs_cap < 0) {
+        set_error("bad pairs output");
+        return SCAN_EINVAL;
+    }
+    SCAN_CUDA(cudaSetDevice(g->ctx->device));
+    return query_pipeline(g, *params, mode, o->core, o->cid, o->label, o->pairs, o->pairs_cap, o->npairs);
+    ABI_GUARD_END
+}
+
+scan_status scan_query_ex(scan_graph *g, const scan_params *params, uint32_t mode, scan_result **out) {
+    ABI_GUARD_BEGIN
+    if (!g || !out) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
+    *out = nullptr;
+    SCAN_TRY(check_params(params));
+    Ctx *c = g->ctx;
+    SCAN_CUDA(cudaSetDevice(c->device));
+    auto *core = (uint8_t *)g->core.ptr;
+    auto *cid = (int32_t *)g->cid.ptr;
+    auto *label = (uint8_t *)g->label.ptr;
+    auto *pairs = (int32_t *)g->pairs.ptr;
+    auto *np = (int64_t *)g->npairs.ptr;
+    SCAN_TRY(query_pipeline(g, *params, mode, core, cid, label, pairs, g->nnz, np));
+    SCAN_CUDA(cudaMemcpyAsync(g->h_npairs, np, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    SCAN_TRY(take_device_error(g));  // synchronises
+    scan_result *r = new scan_result();
+    r->n = g->n;
+    r->k = *g->h_npairs;
+    const size_t n = (size_t)g->n, k = (size_t)r->k;
+    cudaError_t e = cudaMallocHost(&r->core, n + 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&r->cid, 4 * n + 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&r->label, n + 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&r->pairs, 8 * k + 8);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->core, core, n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->cid, cid, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->label, label, n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && k) e = cudaMemcpyAsync(r->pairs, pairs, 8 * k, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        scan_result_free(r);
+        return cuda_fail(e, "result download");
+    }
+    *out = r;
+    return SCAN_OK;
+    ABI_GUARD_END
+}
+
+scan_status scan_query(scan_graph *g, uint32_t eps_num, uint32_t eps_den, uint32_t mu, scan_result **out) {
+    scan_params p{eps_num, eps_den, mu};
+    return scan_query_ex(g, &p, SCAN_Q_AUTO, out);
+}
+
+int32_t scan_result_n(const scan_result *r) { return r ? r->n : 0; }
+const uint8_t *scan_result_core(const scan_result *r) { return r ? r->core : nullptr; }
+const int32_t *scan_result_cluster(const scan_result *r) { return r ? r->cid : nullptr; }
+const uint8_t *scan_result_label(const scan_result *r) { return r ? r->label : nullptr; }
+int64_t scan_result_border_count(const scan_result *r) { return r ? r->k : 0; }
+const int32_t *scan_result_border_pairs(const scan_result *r) { return r ? r->pairs : nullptr; }
+
+void scan_result_free(scan_result *r) {
+    if (!r) return;
+    if (r->core) cudaFreeHost(r->core);
+    if (r->cid) cudaFreeHost(r->cid);
+    if (r->label) cudaFreeHost(r->label);
+    if (r->pairs) cudaFreeHost(r->pairs);
+    delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// scan_internal.cuh -- internal structures and device helpers of libscan.so.
+//
+// Layout in HBM of a resident graph (n vertices, nnz = 2m directed slots):
+//   off   int64[n+1]  CSR offsets (vertex array, Section 4.1)
+//   adj   int32[nnz]  neighbour ids, rows ascending (adjacency array)
+//   src   int32[nnz]  row of each slot (COO expansion of off)
+//   rev   uint32[nnz] slot of (v,u) for the slot of (u,v) (plays the Eid role:
+//                     it ties the two directions of one edge together)
+//   deg   int32[n]
+//   oe    uint32[m]   degree-oriented edges: the slot in the row of the lower
+//                     (deg, id) endpoint, i.e. the degree-oriented edge array
+//                     of Section 4.1 expressed as slot ids
+// Per-query scratch lives on the graph and is reused between queries.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "scan.h"
+
+namespace scan {
+
+// device error word bits
+enum : uint32_t {
+    ERR_UF_LIMIT = 1u,     // union-find retry bound hit
+    ERR_FIND_LIMIT = 2u,   // root walk bound hit
+    ERR_LOOP_LIMIT = 4u,   // any other bounded device loop
+};
+
+constexpr int kWarp = 32;
+
+struct Ctx;
+
+// Device allocation accounted against the context's budget.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Graph {
+    Ctx *ctx = nullptr;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int64_t m = 0;          // undirected edges = nnz / 2
+    DevBuf off, adj, src, rev, deg, oe;
+    DevBuf cn_cache;        // int32[nnz] closed common counts (cached-count serving)
+    bool cache_valid = false;
+    // per-query scratch
+    DevBuf sim;             // uint8[nnz] 1 = eps-similar
+    DevBuf core, cid, parent, label;
+    DevBuf cnt, cnt_off;    // int32[n+1] counts, int64[n+1] exclusive offsets
+    DevBuf ucnt, pair_off;  // unique membership counts / offsets
+    DevBuf raw;             // int32[nnz] raw border candidates
+    DevBuf pairs;           // int32[2*nnz]
+    DevBuf npairs;          // int64[1]
+    DevBuf scan_tmp;        // block partials for the prefix scan
+    DevBuf err;             // uint32[1]
+    // host staging
+    int64_t *h_npairs = nullptr; // pinned
+    uint32_t *h_err = nullptr;   // pinned
+};
+
+struct StageMark {
+    int stage;
+    cudaEvent_t start, stop;
+};
+
+struct Ctx {
+    int device = 0;
+    uint64_t budget = 0;   // 0 = no cap
+    uint64_t used = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t launches = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    // per-stage timing
+    bool profiling = false;
+    std::vector<StageMark> marks;
+    double stage_ms[SCAN_STAGE_COUNT] = {0};
+    int64_t stage_n[SCAN_STAGE_COUNT] = {0};
+};
+
+// Records CUDA events around one stage when the context is profiling.
+struct StageTimer {
+    Ctx *c;
+    StageMark mark{};
+    bool on;
+    StageTimer(Ctx *ctx, int stage) : c(ctx), on(ctx->profiling) {
+        if (!on) return;
+        mark.stage = stage;
+        cudaEventCreate(&mark.start);
+        cudaEventCreate(&mark.stop);
+        cudaEventRecord(mark.start, c->stream);
+    }
+    ~StageTimer() {
+        if (!on) return;
+        cudaEventRecord(mark.stop, c->stream);
+        c->marks.push_back(mark);
+    }
+};
+
+// ---- host helpers (abi.cu)
+void set_error(const std::string &msg);
+scan_status cuda_fail(cudaError_t e, const char *what);
+scan_status dev_alloc(Ctx *c, DevBuf &b, size_t bytes);
+void dev_free(Ctx *c, DevBuf &b);
+
+#define SCAN_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return ::scan::cuda_fail(_e, #call);  \
+    } while (0)
+
+#define SCAN_TRY(call)                       \
+    do {                                     \
+        scan_status _s = (call);             \
+        if (_s != SCAN_OK) return _s;        \
+    } while (0)
+
+// ---- launchers (k_*.cu); every launcher counts its kernels in ctx->launches
+scan_status launch_exclusive_scan_i32_to_i64(Ctx *c, const int32_t *in, int64_t *out, int64_t count,
+                                             DevBuf &tmp);
+scan_status graph_prepare(Graph *g);                    // deg, src, rev, validation, oe
+scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_t *core, int32_t *cid,
+                           uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs);
+scan_status build_count_cache(Graph *g);
+
+inline unsigned grid_for(int64_t items, int per_block, int max_blocks = 1 << 30) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+}  // namespace scan
+
+// ---------------------------------------------------------------- device
+namespace scan {
+namespace dev {
+
+// Exact eps-test of Definition 2.3 with eps = p/q on closed sizes:
+// sigma(u,v) >= p/q  <=>  c^2 q^2 >= p^2 du dv  (c < 2^31, du dv < 2^62).
+__device__ __forceinline__ bool eps_similar(uint64_t c, uint64_t du1, uint64_t dv1, uint64_t pp, uint64_t qq) {
+    unsigned __int128 lhs = (unsigned __int128)(c * c) * qq;
+    unsigned __int128 rhs = (unsigned __int128)pp * (du1 * dv1);
+    return lhs >= rhs;
+}
+
+// Degree-only outcomes (|N[u] cap N[v]| lies in [2, min(du, dv)]):
+// sigma <= sqrt(dmin/dmax) < eps  <=>  dmin q^2 < p^2 dmax  -> never similar
+__device__ __forceinline__ bool prune_dissimilar(uint64_t dmin1, uint64_t dmax1, uint64_t pp, uint64_t qq) {
+    return (unsigned __int128)dmin1 * qq < (unsigned __int128)pp * dmax1;
+}
+// sigma >= 2/sqrt(du dv) >= eps  <=>  4 q^2 >= p^2 du dv  -> always similar
+__device__ __forceinline__ bool prune_similar(uint64_t du1, uint64_t dv1, uint64_t pp, uint64_t qq) {
+    return (unsigned __int128)4u * qq >= (unsigned __int128)pp * (du1 * dv1);
+}
+
+// (deg, id) orientation of Section 4.1: u precedes v.
+__device__ __forceinline__ bool rank_less(int32_t du, int32_t u, int32_t dv, int32_t v) {
+    return du < dv || (du == dv && u < v);
+}
+
+}  // namespace dev
+}  // namespace scan

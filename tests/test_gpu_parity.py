@@ -1,0 +1,235 @@
+"""GPU path vs the CPU oracle, bit-exact (tolerance 0: no float reaches the output).
+
+Every call goes through the C ABI (libscan.so via the ctypes binding).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from conftest import load_golden
+from scan_checks import assert_same, check_invariants
+
+pytestmark = pytest.mark.gpu
+
+MODES = ("recompute", "plain", "cache")
+
+
+@pytest.fixture(scope="module")
+def ps():
+    from paper_2311_12281_gb300 import _build
+    _build.build()
+    import paper_2311_12281_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(ps):
+    c = ps.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_query(ps, g, p, q, mu, mode):
+    if mode == "recompute":
+        return g.query(p, q, mu, ps.SCAN_Q_RECOMPUTE)
+    if mode == "plain":
+        return g.query(p, q, mu, ps.SCAN_Q_PLAIN)
+    if mode == "cache":
+        if not g.has_cache:
+            return g.query(p, q, mu, ps.SCAN_Q_BUILD_CACHE)
+        return g.query(p, q, mu, ps.SCAN_Q_AUTO)
+    raise ValueError(mode)
+
+
+def check_graph(ps, ctx, graph, params, modes=MODES, invariants=True):
+    dg = ctx.load(graph)
+    try:
+        for (p, q, mu) in params:
+            want = oracle.scan(graph, p, q, mu)
+            for mode in modes:
+                got = gpu_query(ps, dg, p, q, mu, mode)
+                assert_same(got, want, f"{graph.name} eps={p}/{q} mu={mu} mode={mode}")
+        if "cache" in modes and graph.nnz:
+            assert np.array_equal(dg.counts(), oracle.common_counts(graph))
+        if invariants and graph.n <= 20000:
+            cn = oracle.common_counts(graph)
+            p, q, mu = params[0]
+            check_invariants(graph, gpu_query(ps, dg, p, q, mu, "recompute"), cn, p, q, mu)
+    finally:
+        dg.free()
+
+
+def test_fig1_fixture(ps, ctx):
+    gd = load_golden("fig1.txt")
+    e = list(map(int, gd["edges"][0].split()))
+    g = gg.from_edges(int(gd["n"][0]), list(zip(e[0::2], e[1::2])))
+    check_graph(ps, ctx, g, [(3, 5, 3), (1, 2, 2), (4, 5, 4)])
+    dg = ctx.load(g)
+    r = dg.query(3, 5, 3)
+    assert set(np.flatnonzero(r["core"]).tolist()) == set(map(int, gd["core"][0].split()))
+    assert r["label"][8] == 2 and [tuple(x) for x in r["pairs"].tolist()] == [(2, 0)]
+    dg.free()
+
+
+def test_every_small_graph_as_one_disjoint_union(ps, ctx):
+    # all labelled graphs on 4 vertices and a seeded third of those on 5,
+    # concatenated into one graph (the result is the union of the parts)
+    parts = []
+    for n, keep in ((3, 1.0), (4, 1.0), (5, 0.35)):
+        pairs = list(itertools.combinations(range(n), 2))
+        rng = np.random.default_rng(n)
+        for mask in range(1 << len(pairs)):
+            if keep < 1.0 and rng.random() > keep:
+                continue
+            parts.append(gg.from_edges(n, [pairs[k] for k in range(len(pairs)) if mask >> k & 1]))
+    union, _ = gg.disjoint_union(parts)
+    union.name = "small-graph union"
+    params = [(p, q, mu) for (p, q) in [(1, 3), (1, 2), (3, 5), (2, 3), (3, 4), (1, 1)] for mu in (2, 3, 4, 5)]
+    check_graph(ps, ctx, union, params, invariants=False)
+
+
+@pytest.mark.parametrize("family", ["complete", "star", "path", "double_star", "hub_via_border", "no_edges",
+                                    "single_edge"])
+def test_special_families(ps, ctx, family):
+    if family == "complete":
+        g = gg.from_edges(40, [(a, b) for a in range(40) for b in range(a + 1, 40)])
+    elif family == "star":
+        g = gg.from_edges(300, [(0, i) for i in range(1, 300)])
+    elif family == "path":
+        g = gg.from_edges(1000, [(i, i + 1) for i in range(999)])
+    elif family == "double_star":
+        g = gg.from_edges(6, [(0, 1), (0, 2), (0, 3), (1, 4), (1, 5)])
+    elif family == "hub_via_border":
+        g = gg.from_edges(10, [(0, 1), (0, 2), (0, 4), (0, 6), (2, 7), (2, 9), (3, 9), (5, 9), (8, 9)])
+    elif family == "no_edges":
+        g = gg.from_edges(7, [])
+    else:
+        g = gg.from_edges(2, [(0, 1)])
+    g.name = family
+    check_graph(ps, ctx, g, [(1, 2, 2), (2, 3, 3), (501, 1000, 3), (2, 5, 5), (1, 1, 2), (1, 5, 10)])
+
+
+def test_empty_graph(ps, ctx):
+    g = gg.from_csr(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    dg = ctx.load(g)
+    r = dg.query(1, 2, 2)
+    assert len(r["core"]) == 0 and len(r["pairs"]) == 0
+    dg.free()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_power_law_graphs(ps, ctx, seed):
+    # sizes chosen to span many thread blocks with ragged tails
+    g = gg.chung_lu([1237, 7919, 30011][seed - 1], [6.0, 17.0, 33.0][seed - 1], 2.1, seed=100 + seed)
+    params = [(p, q, mu) for (p, q) in gg.EPS_SWEEP[::2] for mu in gg.MU_SWEEP]
+    check_graph(ps, ctx, g, params)
+
+
+def test_rmat_scale14_full_sweep(ps, ctx):
+    g = gg.rmat_s14()
+    params = [(p, q, mu) for (p, q) in gg.EPS_SWEEP for mu in gg.MU_SWEEP]
+    check_graph(ps, ctx, g, params)
+
+
+def test_query_entry_points_agree(ps, ctx):
+    g = gg.rmat(12, 16, seed=9)
+    dg = ctx.load(g)
+    a = ps.scan_query(dg.handle, 2, 5, 4)
+    assert_same(a, oracle.scan(g, 2, 5, 4))
+    dg.free()
+
+
+def test_device_resident_query(ps, ctx):
+    torch = pytest.importorskip("torch")
+    g = gg.chung_lu(5000, 12.0, 2.1, seed=77)
+    off = torch.from_numpy(g.offsets).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    torch.cuda.synchronize()
+    h = ps.scan_graph_load(ctx.handle, g.n, off.data_ptr(), adj.data_ptr(), g.nnz, ps.SCAN_LOAD_DEVICE_PTRS)
+    core = torch.zeros(g.n, dtype=torch.uint8, device="cuda")
+    cid = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    label = torch.zeros(g.n, dtype=torch.uint8, device="cuda")
+    pairs = torch.zeros(2 * g.nnz, dtype=torch.int32, device="cuda")
+    npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ps.scan_query_device(h, 1, 2, 3, ps.SCAN_Q_RECOMPUTE, core.data_ptr(), cid.data_ptr(), label.data_ptr(),
+                         pairs.data_ptr(), g.nnz, npairs.data_ptr())
+    ps.scan_ctx_sync(ctx.handle)
+    k = int(npairs.item())
+    got = {"core": core.cpu().numpy(), "cid": cid.cpu().numpy(), "label": label.cpu().numpy(),
+           "pairs": pairs[: 2 * k].cpu().numpy().reshape(k, 2)}
+    assert_same(got, oracle.scan(g, 1, 2, 3))
+    ps.scan_graph_free(h)
+
+
+def test_cache_lifecycle(ps, ctx):
+    g = gg.chung_lu(4000, 20.0, 2.1, seed=8)
+    dg = ctx.load(g)
+    assert not dg.has_cache
+    with pytest.raises(ps.ScanError):
+        dg.counts()
+    r1 = dg.query(3, 10, 3, ps.SCAN_Q_BUILD_CACHE)
+    assert dg.has_cache
+    for (p, q, mu) in [(1, 5, 2), (3, 10, 3), (4, 5, 10)]:
+        assert_same(dg.query(p, q, mu), oracle.scan(g, p, q, mu))
+    assert_same(r1, oracle.scan(g, 3, 10, 3))
+    dg.drop_cache()
+    assert not dg.has_cache
+    assert_same(dg.query(1, 5, 2), oracle.scan(g, 1, 5, 2))
+    dg.free()
+
+
+def test_invalid_parameters(ps, ctx):
+    g = gg.from_edges(4, [(0, 1), (1, 2)])
+    dg = ctx.load(g)
+    for (p, q, mu) in [(0, 1, 2), (1, 0, 2), (3, 2, 2), (1, 2, 1)]:
+        with pytest.raises(ps.ScanError) as ei:
+            dg.query(p, q, mu)
+        assert ei.value.status == ps.SCAN_EINVAL
+    dg.free()
+
+
+@pytest.mark.parametrize("case", ["asymmetric", "self_loop", "unsorted", "duplicate", "out_of_range",
+                                  "bad_offsets"])
+def test_malformed_csr_is_rejected(ps, ctx, case):
+    csr = {
+        "asymmetric": ([0, 1, 2, 2], [1, 2]),
+        "self_loop": ([0, 1, 2], [0, 0]),
+        "unsorted": ([0, 2, 3, 4], [2, 1, 0, 0]),
+        "duplicate": ([0, 2, 3, 4], [1, 1, 0, 0]),
+        "out_of_range": ([0, 1, 2], [5, 0]),
+        "bad_offsets": ([0, 2, 1, 2], [1, 2]),
+    }[case]
+    off, adj = np.array(csr[0], np.int64), np.array(csr[1], np.int32)
+    for flags in (0, ps.SCAN_LOAD_DEVICE_PTRS):
+        if flags:
+            torch = pytest.importorskip("torch")
+            o, a = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+            torch.cuda.synchronize()
+            args = (o.data_ptr(), a.data_ptr())
+        else:
+            args = (off, adj)
+        with pytest.raises(ps.ScanError) as ei:
+            ps.scan_graph_load(ctx.handle, len(off) - 1, *args, len(adj), flags)
+        assert ei.value.status == ps.SCAN_EINVAL
+
+
+def test_budget_is_enforced(ps):
+    g = gg.chung_lu(20000, 16.0, 2.1, seed=3)
+    c = ps.Context(0, budget_bytes=1 << 20)
+    with pytest.raises(ps.ScanError) as ei:
+        c.load(g)
+    assert ei.value.status == ps.SCAN_EBUDGET
+    assert c.device_bytes == 0
+    c.close()
+
+
+def test_kernel_launch_counter_moves(ps, ctx):
+    g = gg.chung_lu(3000, 10.0, 2.1, seed=1)
+    dg = ctx.load(g)
+    before = ctx.kernel_launches
+    dg.query(1, 2, 3)
+    assert ctx.kernel_launches > before
+    dg.free()
