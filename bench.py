@@ -207,7 +207,10 @@ def main():
         dist.init_process_group("nccl")
     _build.build()
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library launches on it, and the
+    # CUDA events that time the steps are recorded on it
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
 
     g = make_graph(args.scale)
     dmin1, dmax1 = oriented_dmin(g)

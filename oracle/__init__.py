@@ -53,6 +53,8 @@ def _lib():
         lib.oracle_common_counts.argtypes = [i64, vp, vp, vp, i32]
         lib.oracle_scan.restype = i32
         lib.oracle_scan.argtypes = [i64, vp, vp, u32, u32, u32, i32, vp, vp, vp, vp, vp, vp]
+        lib.oracle_scan_from_counts.restype = i32
+        lib.oracle_scan_from_counts.argtypes = [i64, vp, vp, vp, u32, u32, u32, vp, vp, vp, vp, vp]
         lib.oracle_counts_for_slots.restype = None
         lib.oracle_counts_for_slots.argtypes = [i64, vp, vp, vp, i64, vp, i32]
         lib.brute_scan.restype = i32
@@ -121,6 +123,27 @@ def scan(graph, eps_num: int, eps_den: int, mu: int, threads: int = 0, want_cn: 
     if want_cn:
         out["cn"] = cn[:nnz]
     return out
+
+
+def scan_from_counts(graph, cn: np.ndarray, eps_num: int, eps_den: int, mu: int) -> dict:
+    """SCAN given the per-slot closed common counts (from common_counts)."""
+    off, adj = _csr(graph)
+    n, nnz = graph.n, int(off[-1])
+    c = np.ascontiguousarray(cn, dtype=np.int32)
+    if c.size == 0:
+        c = np.zeros(1, np.int32)
+    core = np.zeros(max(n, 1), dtype=np.uint8)
+    cid = np.zeros(max(n, 1), dtype=np.int32)
+    label = np.zeros(max(n, 1), dtype=np.uint8)
+    pairs = np.zeros(max(2 * nnz, 2), dtype=np.int32)
+    npairs = np.zeros(1, dtype=np.int64)
+    rc = _lib().oracle_scan_from_counts(n, off.ctypes.data, adj.ctypes.data, c.ctypes.data, int(eps_num),
+                                        int(eps_den), int(mu), core.ctypes.data, cid.ctypes.data,
+                                        label.ctypes.data, pairs.ctypes.data, npairs.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_scan_from_counts rejected the input (code {rc})")
+    k = int(npairs[0])
+    return {"core": core[:n], "cid": cid[:n], "label": label[:n], "pairs": pairs[: 2 * k].reshape(k, 2)}
 
 
 def brute(n: int, edges, eps_num: int, eps_den: int, mu: int) -> dict:

@@ -188,6 +188,10 @@ static int64_t sort_unique(int32_t *a, int64_t k) {
  *   cn_out    : optional per-slot |N[u] cap N[v]| (NULL to skip).
  * threads only parallelises the common-count loop (deterministic).
  */
+int oracle_scan_from_counts(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *cn, uint32_t p,
+                            uint32_t q, uint32_t mu, uint8_t *core, int32_t *cid, uint8_t *label, int32_t *pairs,
+                            int64_t *npairs);
+
 int oracle_scan(int64_t n, const int64_t *off, const int32_t *adj, uint32_t p, uint32_t q, uint32_t mu,
                 int threads, uint8_t *core, int32_t *cid, uint8_t *label, int32_t *pairs, int64_t *npairs,
                 int32_t *cn_out) {
@@ -195,20 +199,35 @@ int oracle_scan(int64_t n, const int64_t *off, const int32_t *adj, uint32_t p, u
     if (p == 0 || q == 0 || p > q || mu < 2) return ORACLE_EINVAL;
     int64_t nnz = off[n], bad;
     if (oracle_validate(n, off, adj, nnz, &bad) != ORACLE_OK) return ORACLE_EINVAL;
-
     int32_t *cn = cn_out ? cn_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!cn) return ORACLE_ENOMEM;
+
+    /* Definition 2.2: common closed-neighbour counts per adjacent pair */
+    oracle_common_counts(n, off, adj, cn, threads);
+
+    int rc = oracle_scan_from_counts(n, off, adj, cn, p, q, mu, core, cid, label, pairs, npairs);
+    if (!cn_out) free(cn);
+    return rc;
+}
+
+/*
+ * The rest of SCAN(eps = p/q, mu) once the per-slot closed common counts
+ * cn[nnz] of Definition 2.2 are known (outputs as for oracle_scan).
+ */
+int oracle_scan_from_counts(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *cn, uint32_t p,
+                            uint32_t q, uint32_t mu, uint8_t *core, int32_t *cid, uint8_t *label, int32_t *pairs,
+                            int64_t *npairs) {
+    *npairs = 0;
+    if (p == 0 || q == 0 || p > q || mu < 2) return ORACLE_EINVAL;
+    int64_t nnz = off[n];
     uint8_t *sim = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
     int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int64_t *boff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int32_t *scratch = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
-    if (!cn || !sim || !queue || !boff || !scratch) {
-        if (!cn_out) free(cn);
+    if (!sim || !queue || !boff || !scratch) {
         free(sim); free(queue); free(boff); free(scratch);
         return ORACLE_ENOMEM;
     }
-
-    /* Definition 2.2: common closed-neighbour counts per adjacent pair */
-    oracle_common_counts(n, off, adj, cn, threads);
 
     /* Definition 2.3: S(u,v) per slot */
     for (int64_t u = 0; u < n; ++u)
@@ -284,7 +303,6 @@ int oracle_scan(int64_t n, const int64_t *off, const int32_t *adj, uint32_t p, u
         label[u] = (uint8_t)(k >= 2 ? LABEL_HUB : LABEL_OUTLIER);
     }
 
-    if (!cn_out) free(cn);
     free(sim); free(queue); free(boff); free(scratch);
     return ORACLE_OK;
 }

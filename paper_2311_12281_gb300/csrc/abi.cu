@@ -52,10 +52,7 @@ void dev_free(Ctx *c, DevBuf &b) {
 
 static void graph_release(Graph *g) {
     Ctx *c = g->ctx;
-    DevBuf *bufs[] = {&g->off, &g->adj, &g->src, &g->rev, &g->deg, &g->oe, &g->cn_cache, &g->sim,
-                      &g->core, &g->cid, &g->parent, &g->label, &g->cnt, &g->cnt_off, &g->ucnt,
-                      &g->pair_off, &g->raw, &g->pairs, &g->npairs, &g->scan_tmp, &g->err};
-    for (DevBuf *b : bufs) dev_free(c, *b);
+    g->for_each_buf([c](DevBuf &b) { dev_free(c, b); });
     if (g->h_npairs) cudaFreeHost(g->h_npairs);
     if (g->h_err) cudaFreeHost(g->h_err);
     g->h_npairs = nullptr;
@@ -287,11 +284,8 @@ int64_t scan_graph_nnz(const scan_graph *g) { return g ? g->nnz : 0; }
 
 uint64_t scan_graph_device_bytes(const scan_graph *g) {
     if (!g) return 0;
-    const DevBuf *bufs[] = {&g->off, &g->adj, &g->src, &g->rev, &g->deg, &g->oe, &g->cn_cache, &g->sim,
-                            &g->core, &g->cid, &g->parent, &g->label, &g->cnt, &g->cnt_off, &g->ucnt,
-                            &g->pair_off, &g->raw, &g->pairs, &g->npairs, &g->scan_tmp, &g->err};
     uint64_t s = 0;
-    for (const DevBuf *b : bufs) s += b->bytes;
+    const_cast<scan_graph *>(g)->for_each_buf([&s](DevBuf &b) { s += b.bytes; });
     return s;
 }
 

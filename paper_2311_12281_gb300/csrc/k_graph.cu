@@ -162,7 +162,7 @@ scan_status graph_prepare(Graph *g) {
         c->launches++;
     }
     SCAN_CUDA(cudaGetLastError());
-    return SCAN_OK;
+    return owner_schedule_build(g);
 }
 
 }  // namespace scan

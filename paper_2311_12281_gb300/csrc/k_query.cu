@@ -300,7 +300,7 @@ static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write
 scan_status build_count_cache(Graph *g) {
     Ctx *c = g->ctx;
     if (!g->cn_cache.ptr) SCAN_TRY(dev_alloc(c, g->cn_cache, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
-    SCAN_TRY(launch_isect(g, false, false, true, 0, 0, (int32_t *)g->cn_cache.ptr));
+    SCAN_TRY(launch_owner_isect(g, false, false, true, 0, 0, (int32_t *)g->cn_cache.ptr));
     g->cache_valid = true;
     return SCAN_OK;
 }
@@ -335,7 +335,7 @@ scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_
         } else if (mode & SCAN_Q_PLAIN) {
             SCAN_TRY(launch_isect(g, false, true, false, pp, qq, nullptr));
         } else {
-            SCAN_TRY(launch_isect(g, true, true, false, pp, qq, nullptr));
+            SCAN_TRY(launch_owner_isect(g, true, true, false, pp, qq, nullptr));
         }
     }
 

@@ -48,6 +48,14 @@ struct Graph {
     DevBuf off, adj, src, rev, deg, oe;
     DevBuf cn_cache;        // int32[nnz] closed common counts (cached-count serving)
     bool cache_valid = false;
+    // owner schedule of the shared-memory intersection (built at load)
+    DevBuf owners_small;    // int32[n_small] owners with deg <= 128
+    DevBuf items[4];        // work items of classes 1..3
+    int64_t n_items[4] = {0, 0, 0, 0};
+    int32_t n_small = 0;
+    DevBuf owners_chunked;  // int32[n_chunked] owners whose row is split in value chunks
+    int32_t n_chunked = 0;
+    DevBuf acc;             // int32[nnz] partial counts of chunked owners (kept zero between queries)
     // per-query scratch
     DevBuf sim;             // uint8[nnz] 1 = eps-similar
     DevBuf core, cid, parent, label;
@@ -61,6 +69,14 @@ struct Graph {
     // host staging
     int64_t *h_npairs = nullptr; // pinned
     uint32_t *h_err = nullptr;   // pinned
+
+    template <class F>
+    void for_each_buf(F f) {
+        DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
+                          &items[2], &items[3], &owners_chunked, &acc, &sim, &core, &cid, &parent, &label,
+                          &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
+        for (DevBuf *b : bufs) f(*b);
+    }
 };
 
 struct StageMark {
@@ -128,6 +144,9 @@ scan_status graph_prepare(Graph *g);                    // deg, src, rev, valida
 scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_t *core, int32_t *cid,
                            uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs);
 scan_status build_count_cache(Graph *g);
+scan_status owner_schedule_build(Graph *g);
+scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, uint64_t pp, uint64_t qq,
+                               int32_t *cn);
 
 inline unsigned grid_for(int64_t items, int per_block, int max_blocks = 1 << 30) {
     int64_t b = (items + per_block - 1) / per_block;
