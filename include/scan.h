@@ -189,6 +189,37 @@ typedef struct scan_device_out {
 
 SCAN_API scan_status scan_query_device(scan_graph *g, const scan_params *params, uint32_t mode, const scan_device_out *out);
 
+/* --------------------------------------------------------------- batch */
+/*
+ * Many independent graphs clustered together (each with its own eps, mu).
+ * The k graphs are kept on the device as one disjoint union; since no edge
+ * joins two graphs, one pass over the union answers all k queries, every
+ * pipeline stage being a single launch over all of them. Each result equals
+ * the single-graph result (ids local to its graph). Not in the paper: its
+ * algorithms take one graph at a time (Algorithm 1).
+ */
+typedef struct scan_batch scan_batch;
+
+/* Host CSRs of k graphs (n[j], offsets[j] int64[n[j]+1], adj[j] int32[...]),
+ * each under scan_graph_load's contract; flags must be 0. The union must stay
+ * below 2^31 vertices and 2^32 slots. Errors as scan_graph_load. */
+SCAN_API scan_status scan_batch_load(scan_ctx *ctx, int32_t k, const int32_t *n, const int64_t *const *offsets,
+                                     const int32_t *const *adj, uint32_t flags, scan_batch **out);
+SCAN_API int32_t scan_batch_size(const scan_batch *b);
+/* The resident union as a graph handle (owned by the batch; do not free). */
+SCAN_API scan_graph *scan_batch_union(scan_batch *b);
+/* params[k]: graph j's eps, mu. outs[k] receive one result per graph (each
+ * freed with scan_result_free). On failure no result is returned. */
+SCAN_API scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t mode, scan_result **outs);
+/* Device-resident form: writes the union's result (union ids) into device
+ * buffers sized for the union, on the context's stream, without syncing. */
+SCAN_API scan_status scan_batch_query_device(scan_batch *b, const scan_params *params, uint32_t mode,
+                                             const scan_device_out *out);
+SCAN_API void scan_batch_free(scan_batch *b);
+/* One-call form over graphs loaded separately in one context: builds a
+ * temporary union, answers all k queries (full recompute) and frees it. */
+SCAN_API scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs);
+
 #ifdef __cplusplus
 }
 #endif

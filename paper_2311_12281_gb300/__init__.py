@@ -74,6 +74,13 @@ SIGNATURES = {
     "scan_query": (ctypes.c_int, [_VP, _U32, _U32, _U32, _PP]),
     "scan_query_ex": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, _PP]),
     "scan_query_device": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, ctypes.POINTER(scan_device_out)]),
+    "scan_batch_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _U32, _PP]),
+    "scan_batch_size": (_I32, [_VP]),
+    "scan_batch_union": (_VP, [_VP]),
+    "scan_batch_query": (ctypes.c_int, [_VP, _VP, _U32, _VP]),
+    "scan_batch_query_device": (ctypes.c_int, [_VP, _VP, _U32, ctypes.POINTER(scan_device_out)]),
+    "scan_batch_free": (None, [_VP]),
+    "scan_query_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "scan_result_n": (_I32, [_VP]),
     "scan_result_core": (_VP, [_VP]),
     "scan_result_cluster": (_VP, [_VP]),
@@ -238,6 +245,62 @@ def scan_query_device(g: int, eps_num: int, eps_den: int, mu: int, mode: int, co
     p = scan_params(eps_num, eps_den, mu)
     o = scan_device_out(core, cid, label, pairs, pairs_cap, npairs)
     _check(lib().scan_query_device(g, ctypes.byref(p), mode, ctypes.byref(o)))
+
+
+def _params_array(params):
+    arr = (scan_params * len(params))()
+    for j, (p, q, mu) in enumerate(params):
+        arr[j] = scan_params(int(p), int(q), int(mu))
+    return arr
+
+
+def scan_batch_load(ctx: int, graphs, flags: int = 0) -> int:
+    """graphs: objects with n, offsets (int64), adj (int32) host arrays."""
+    k = len(graphs)
+    offs = [np.ascontiguousarray(g.offsets, dtype=np.int64) for g in graphs]
+    adjs = [np.ascontiguousarray(g.adj, dtype=np.int32) for g in graphs]
+    ns = np.asarray([g.n for g in graphs], dtype=np.int32)
+    po = (ctypes.c_void_p * k)(*[o.ctypes.data for o in offs])
+    pa = (ctypes.c_void_p * k)(*[a.ctypes.data if a.size else None for a in adjs])
+    out = ctypes.c_void_p()
+    _check(lib().scan_batch_load(ctx, k, ns.ctypes.data, po, pa, int(flags), ctypes.byref(out)))
+    return out.value
+
+
+def scan_batch_size(b: int) -> int:
+    return int(lib().scan_batch_size(b))
+
+
+def scan_batch_union(b: int) -> int:
+    return lib().scan_batch_union(b)
+
+
+def scan_batch_free(b: int):
+    lib().scan_batch_free(b)
+
+
+def scan_batch_query(b: int, params, mode: int = SCAN_Q_RECOMPUTE) -> list:
+    """params: [(eps_num, eps_den, mu)] per graph; returns one result dict per graph."""
+    k = scan_batch_size(b)
+    assert len(params) == k
+    outs = (ctypes.c_void_p * k)()
+    _check(lib().scan_batch_query(b, _params_array(params), mode, outs))
+    return [_result_to_numpy(outs[j]) for j in range(k)]
+
+
+def scan_batch_query_device(b: int, params, mode: int, core: int, cid: int, label: int, pairs: int,
+                            pairs_cap: int, npairs: int):
+    o = scan_device_out(core, cid, label, pairs, pairs_cap, npairs)
+    _check(lib().scan_batch_query_device(b, _params_array(params), mode, ctypes.byref(o)))
+
+
+def scan_query_batch(graphs, params) -> list:
+    """graphs: scan_graph handles of one context; one full-recompute result per graph."""
+    k = len(graphs)
+    gs = (ctypes.c_void_p * k)(*graphs)
+    outs = (ctypes.c_void_p * k)()
+    _check(lib().scan_query_batch(gs, _params_array(params), k, outs))
+    return [_result_to_numpy(outs[j]) for j in range(k)]
 
 
 # --------------------------------------------------------------- convenience

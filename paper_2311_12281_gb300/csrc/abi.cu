@@ -59,7 +59,7 @@ static void graph_release(Graph *g) {
     g->h_err = nullptr;
 }
 
-static scan_status check_params(const scan_params *p) {
+scan_status check_params(const scan_params *p) {
     if (!p) { set_error("params is NULL"); return SCAN_EINVAL; }
     if (p->eps_num == 0 || p->eps_den == 0 || p->eps_num > p->eps_den) {
         set_error("eps must satisfy 0 < eps_num <= eps_den (0 < eps <= 1)");
@@ -70,7 +70,7 @@ static scan_status check_params(const scan_params *p) {
 }
 
 // Reads and clears the graph's device error word after a synchronisation.
-static scan_status take_device_error(Graph *g) {
+scan_status take_device_error(Graph *g) {
     Ctx *c = g->ctx;
     SCAN_CUDA(cudaMemcpyAsync(g->h_err, g->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     SCAN_CUDA(cudaStreamSynchronize(c->stream));
@@ -87,16 +87,6 @@ static scan_status take_device_error(Graph *g) {
 
 using namespace scan;
 
-struct scan_ctx : Ctx {};
-struct scan_graph : Graph {};
-struct scan_result {
-    int32_t n = 0;
-    int64_t k = 0;
-    uint8_t *core = nullptr;
-    int32_t *cid = nullptr;
-    uint8_t *label = nullptr;
-    int32_t *pairs = nullptr;
-};
 
 #define ABI_GUARD_BEGIN try {
 #define ABI_GUARD_END                                   \
@@ -206,10 +196,12 @@ scan_status scan_ctx_stage_time(scan_ctx *c, int32_t stage, double *total_ms, in
     return SCAN_OK;
 }
 
-scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
-                            uint32_t flags, scan_graph **out) {
-    ABI_GUARD_BEGIN
-    if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
+}  // extern "C"
+
+namespace scan {
+
+scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, bool on_dev,
+                         Graph **out) {
     *out = nullptr;
     if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj)) {
         set_error("bad sizes or NULL arrays");
@@ -221,11 +213,6 @@ scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, co
         set_error("a resident graph needs nnz < 2^32 (use SCAN_LOAD_PINNED_BORROW)");
         return SCAN_EINVAL;
     }
-    if (flags & SCAN_LOAD_PINNED_BORROW) {
-        set_error("SCAN_LOAD_PINNED_BORROW is not available in this build");
-        return SCAN_EINVAL;
-    }
-    const bool on_dev = flags & SCAN_LOAD_DEVICE_PTRS;
     if (!on_dev && n > 0) {  // cheap host-side check before any copy
         if (offsets[0] != 0 || offsets[n] != nnz) {
             set_error("offsets[0] must be 0 and offsets[n] must equal nnz");
@@ -268,16 +255,65 @@ scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, co
     if (e != cudaSuccess) return fail(cuda_fail(e, "graph prepare"));
     *out = g;
     return SCAN_OK;
-    ABI_GUARD_END
 }
 
-void scan_graph_free(scan_graph *g) {
+void graph_destroy(Graph *g) {
     if (!g) return;
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     graph_release(g);
-    delete g;
+    delete static_cast<scan_graph *>(g);
 }
+
+scan_result *result_new(int32_t n, int64_t k, bool pinned) {
+    scan_result *r = new scan_result();
+    r->n = n;
+    r->k = k;
+    r->pinned = pinned;
+    const size_t bn = (size_t)n + 1, bk = 8 * (size_t)k + 8;
+    if (pinned) {
+        cudaError_t e = cudaMallocHost(&r->core, bn);
+        if (e == cudaSuccess) e = cudaMallocHost(&r->cid, 4 * bn);
+        if (e == cudaSuccess) e = cudaMallocHost(&r->label, bn);
+        if (e == cudaSuccess) e = cudaMallocHost(&r->pairs, bk);
+        if (e != cudaSuccess) {
+            scan_result_free(r);
+            return nullptr;
+        }
+    } else {
+        r->core = (uint8_t *)malloc(bn);
+        r->cid = (int32_t *)malloc(4 * bn);
+        r->label = (uint8_t *)malloc(bn);
+        r->pairs = (int32_t *)malloc(bk);
+        if (!r->core || !r->cid || !r->label || !r->pairs) {
+            scan_result_free(r);
+            return nullptr;
+        }
+    }
+    return r;
+}
+
+}  // namespace scan
+
+extern "C" {
+
+scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                            uint32_t flags, scan_graph **out) {
+    ABI_GUARD_BEGIN
+    if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
+    *out = nullptr;
+    if (flags & SCAN_LOAD_PINNED_BORROW) {
+        set_error("SCAN_LOAD_PINNED_BORROW is not available in this build");
+        return SCAN_EINVAL;
+    }
+    Graph *g = nullptr;
+    SCAN_TRY(graph_create(ctx, n, offsets, adj, nnz, (flags & SCAN_LOAD_DEVICE_PTRS) != 0, &g));
+    *out = static_cast<scan_graph *>(g);
+    return SCAN_OK;
+    ABI_GUARD_END
+}
+
+void scan_graph_free(scan_graph *g) { graph_destroy(g); }
 
 int32_t scan_graph_n(const scan_graph *g) { return g ? g->n : 0; }
 int64_t scan_graph_nnz(const scan_graph *g) { return g ? g->nnz : 0; }
@@ -321,7 +357,7 @@ scan_status scan_query_device(scan_graph *g, const scan_params *params, uint32_t
         return SCAN_EINVAL;
     }
     SCAN_CUDA(cudaSetDevice(g->ctx->device));
-    return query_pipeline(g, *params, mode, o->core, o->cid, o->label, o->pairs, o->pairs_cap, o->npairs);
+    return query_pipeline(g, uniform_params(*params), mode, o->core, o->cid, o->label, o->pairs, o->pairs_cap, o->npairs);
     ABI_GUARD_END
 }
 
@@ -337,17 +373,13 @@ scan_status scan_query_ex(scan_graph *g, const scan_params *params, uint32_t mod
     auto *label = (uint8_t *)g->label.ptr;
     auto *pairs = (int32_t *)g->pairs.ptr;
     auto *np = (int64_t *)g->npairs.ptr;
-    SCAN_TRY(query_pipeline(g, *params, mode, core, cid, label, pairs, g->nnz, np));
+    SCAN_TRY(query_pipeline(g, uniform_params(*params), mode, core, cid, label, pairs, g->nnz, np));
     SCAN_CUDA(cudaMemcpyAsync(g->h_npairs, np, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
     SCAN_TRY(take_device_error(g));  // synchronises
-    scan_result *r = new scan_result();
-    r->n = g->n;
-    r->k = *g->h_npairs;
-    const size_t n = (size_t)g->n, k = (size_t)r->k;
-    cudaError_t e = cudaMallocHost(&r->core, n + 1);
-    if (e == cudaSuccess) e = cudaMallocHost(&r->cid, 4 * n + 4);
-    if (e == cudaSuccess) e = cudaMallocHost(&r->label, n + 1);
-    if (e == cudaSuccess) e = cudaMallocHost(&r->pairs, 8 * k + 8);
+    const size_t n = (size_t)g->n, k = (size_t)*g->h_npairs;
+    scan_result *r = result_new(g->n, (int64_t)k, true);
+    if (!r) { set_error("pinned result allocation failed"); return SCAN_ENOMEM; }
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->core, core, n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->cid, cid, 4 * n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(r->label, label, n, cudaMemcpyDeviceToHost, c->stream);
@@ -376,10 +408,12 @@ const int32_t *scan_result_border_pairs(const scan_result *r) { return r ? r->pa
 
 void scan_result_free(scan_result *r) {
     if (!r) return;
-    if (r->core) cudaFreeHost(r->core);
-    if (r->cid) cudaFreeHost(r->cid);
-    if (r->label) cudaFreeHost(r->label);
-    if (r->pairs) cudaFreeHost(r->pairs);
+    void *bufs[] = {r->core, r->cid, r->label, r->pairs};
+    for (void *b : bufs) {
+        if (!b) continue;
+        if (r->pinned) cudaFreeHost(b);
+        else free(b);
+    }
     delete r;
 }
 

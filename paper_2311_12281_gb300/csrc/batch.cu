@@ -1,0 +1,308 @@
+// batch.cu -- many graphs clustered together.
+//
+// A batch stores its k graphs as one resident disjoint union (vertex ids and
+// slots shifted by per-graph bases) plus a graph index per vertex. SCAN
+// never joins vertices of different graphs -- no edge crosses them -- so one
+// query over the union, with each vertex reading its own graph's (eps, mu)
+// through the graph index, answers all k queries at once: every pipeline
+// stage is a single launch over all graphs, and the owner schedule of the
+// union is the work queue over (graph, owner, slot range) items. Results are
+// split per graph on the host, with ids shifted back.
+#include <algorithm>
+#include <vector>
+
+#include "scan_internal.cuh"
+
+using namespace scan;
+
+struct scan_batch {
+    Ctx *ctx = nullptr;
+    Graph *g = nullptr;  // the union
+    int32_t k = 0;
+    std::vector<int64_t> vbase, ebase;  // k+1 each
+    DevBuf gid, gpp, gqq, gmu;
+    uint64_t *h_pp = nullptr, *h_qq = nullptr;  // pinned parameter staging
+    uint32_t *h_mu = nullptr;
+    // pinned download staging for the union result
+    uint8_t *h_core = nullptr, *h_label = nullptr;
+    int32_t *h_cid = nullptr, *h_pairs = nullptr;
+    int64_t h_pairs_cap = 0;
+};
+
+namespace scan {
+namespace {
+
+__global__ void k_graph_index(const int64_t *__restrict__ vbase, int32_t k, int32_t n, int32_t *__restrict__ gid) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t lo = 0, hi = k;  // last j with vbase[j] <= v
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (vbase[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    gid[v] = lo;
+}
+
+void batch_release(scan_batch *b) {
+    if (!b) return;
+    if (b->g) graph_destroy(b->g);
+    b->g = nullptr;
+    DevBuf *bufs[] = {&b->gid, &b->gpp, &b->gqq, &b->gmu};
+    for (DevBuf *d : bufs) dev_free(b->ctx, *d);
+    void *pin[] = {b->h_pp, b->h_qq, b->h_mu, b->h_core, b->h_label, b->h_cid, b->h_pairs};
+    for (void *p : pin)
+        if (p) cudaFreeHost(p);
+    delete b;
+}
+
+scan_status batch_query_to_device(scan_batch *b, const scan_params *params, uint32_t mode, uint8_t *core,
+                                  int32_t *cid, uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs) {
+    Ctx *c = b->ctx;
+    for (int32_t j = 0; j < b->k; ++j) {
+        SCAN_TRY(check_params(params + j));
+        b->h_pp[j] = (uint64_t)params[j].eps_num * params[j].eps_num;
+        b->h_qq[j] = (uint64_t)params[j].eps_den * params[j].eps_den;
+        b->h_mu[j] = params[j].mu;
+    }
+    SCAN_CUDA(cudaMemcpyAsync(b->gpp.ptr, b->h_pp, 8 * (size_t)b->k, cudaMemcpyHostToDevice, c->stream));
+    SCAN_CUDA(cudaMemcpyAsync(b->gqq.ptr, b->h_qq, 8 * (size_t)b->k, cudaMemcpyHostToDevice, c->stream));
+    SCAN_CUDA(cudaMemcpyAsync(b->gmu.ptr, b->h_mu, 4 * (size_t)b->k, cudaMemcpyHostToDevice, c->stream));
+    QParams qp;
+    qp.gid = (const int32_t *)b->gid.ptr;
+    qp.gpp = (const uint64_t *)b->gpp.ptr;
+    qp.gqq = (const uint64_t *)b->gqq.ptr;
+    qp.gmu = (const uint32_t *)b->gmu.ptr;
+    return query_pipeline(b->g, qp, mode, core, cid, label, pairs, pairs_cap, npairs);
+}
+
+}  // namespace
+
+scan_status batch_create(Ctx *ctx, int32_t k, const int32_t *ns, const int64_t *const *offsets,
+                         const int32_t *const *adjs, scan_batch **out) {
+    *out = nullptr;
+    if (k < 1 || !ns || !offsets || !adjs) {
+        set_error("a batch needs k >= 1 graphs");
+        return SCAN_EINVAL;
+    }
+    scan_batch *b = new scan_batch();
+    b->ctx = ctx;
+    b->k = k;
+    b->vbase.assign((size_t)k + 1, 0);
+    b->ebase.assign((size_t)k + 1, 0);
+    auto fail = [&](scan_status s) {
+        batch_release(b);
+        return s;
+    };
+    for (int32_t j = 0; j < k; ++j) {
+        if (ns[j] < 0 || (ns[j] > 0 && (!offsets[j] || offsets[j][0] != 0))) {
+            set_error("graph " + std::to_string(j) + " of the batch has bad offsets");
+            return fail(SCAN_EINVAL);
+        }
+        const int64_t nnz = ns[j] > 0 ? offsets[j][ns[j]] : 0;
+        if (nnz > 0 && !adjs[j]) {
+            set_error("graph " + std::to_string(j) + " of the batch has no adjacency");
+            return fail(SCAN_EINVAL);
+        }
+        b->vbase[j + 1] = b->vbase[j] + ns[j];
+        b->ebase[j + 1] = b->ebase[j] + nnz;
+    }
+    const int64_t n = b->vbase[k], nnz = b->ebase[k];
+    if (n >= (1ll << 31) - 1 || (uint64_t)nnz >= (1ull << 32)) {
+        set_error("the batch union exceeds 2^31 vertices or 2^32 slots");
+        return fail(SCAN_EINVAL);
+    }
+    // the union CSR: shifted offsets and ids
+    std::vector<int64_t> off((size_t)n + 1);
+    std::vector<int32_t> adj((size_t)std::max<int64_t>(nnz, 1));
+    for (int32_t j = 0; j < k; ++j) {
+        const int64_t vb = b->vbase[j], eb = b->ebase[j];
+        for (int32_t i = 0; i < ns[j]; ++i) off[(size_t)(vb + i)] = eb + offsets[j][i];
+        const int64_t m2 = b->ebase[j + 1] - eb;
+        const int32_t *a = adjs[j];
+        int32_t *dst = adj.data() + eb;
+        for (int64_t e = 0; e < m2; ++e) {
+            if (a[e] < 0 || a[e] >= ns[j]) {
+                set_error("graph " + std::to_string(j) + " of the batch: id out of range at slot " + std::to_string(e));
+                return fail(SCAN_EINVAL);
+            }
+            dst[e] = a[e] + (int32_t)vb;
+        }
+    }
+    off[(size_t)n] = nnz;
+    {
+        const scan_status gs = graph_create(ctx, (int32_t)n, off.data(), adj.data(), nnz, false, &b->g);
+        if (gs != SCAN_OK) return fail(gs);
+    }
+    // graph index of every vertex
+    DevBuf dvb;
+    scan_status s = dev_alloc(ctx, dvb, 8 * ((size_t)k + 1));
+    if (s == SCAN_OK) s = dev_alloc(ctx, b->gid, 4 * ((size_t)n + 1));
+    if (s == SCAN_OK) s = dev_alloc(ctx, b->gpp, 8 * (size_t)k);
+    if (s == SCAN_OK) s = dev_alloc(ctx, b->gqq, 8 * (size_t)k);
+    if (s == SCAN_OK) s = dev_alloc(ctx, b->gmu, 4 * (size_t)k);
+    if (s != SCAN_OK) {
+        dev_free(ctx, dvb);
+        return fail(s);
+    }
+    cudaError_t e = cudaMemcpyAsync(dvb.ptr, b->vbase.data(), 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && n > 0) {
+        k_graph_index<<<grid_for(n, 256), 256, 0, ctx->stream>>>((const int64_t *)dvb.ptr, k, (int32_t)n,
+                                                                 (int32_t *)b->gid.ptr);
+        ctx->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, dvb);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_pp, 8 * (size_t)k);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_qq, 8 * (size_t)k);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_mu, 4 * (size_t)k);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_core, (size_t)n + 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_label, (size_t)n + 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_cid, 4 * ((size_t)n + 1));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "batch setup"));
+    *out = b;
+    return SCAN_OK;
+}
+
+}  // namespace scan
+
+extern "C" {
+
+scan_status scan_batch_load(scan_ctx *ctx, int32_t k, const int32_t *n, const int64_t *const *offsets,
+                            const int32_t *const *adj, uint32_t flags, scan_batch **out) {
+    try {
+        if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
+        *out = nullptr;
+        if (flags != 0) { set_error("scan_batch_load takes host arrays only (flags must be 0)"); return SCAN_EINVAL; }
+        SCAN_CUDA(cudaSetDevice(((Ctx *)ctx)->device));
+        return batch_create((Ctx *)ctx, k, n, offsets, adj, out);
+    } catch (...) {
+        set_error("host allocation failed");
+        return SCAN_ENOMEM;
+    }
+}
+
+int32_t scan_batch_size(const scan_batch *b) { return b ? b->k : 0; }
+
+scan_graph *scan_batch_union(scan_batch *b) { return b ? (scan_graph *)b->g : nullptr; }
+
+void scan_batch_free(scan_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    batch_release(b);
+}
+
+scan_status scan_batch_query_device(scan_batch *b, const scan_params *params, uint32_t mode,
+                                    const scan_device_out *o) {
+    try {
+        if (!b || !params || !o) { set_error("NULL argument"); return SCAN_EINVAL; }
+        if (!o->npairs || (!o->core && b->g->n > 0)) { set_error("bad device outputs"); return SCAN_EINVAL; }
+        SCAN_CUDA(cudaSetDevice(b->ctx->device));
+        return batch_query_to_device(b, params, mode, o->core, o->cid, o->label, o->pairs, o->pairs_cap, o->npairs);
+    } catch (...) {
+        set_error("internal error");
+        return SCAN_EINVAL;
+    }
+}
+
+scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t mode, scan_result **outs) {
+    try {
+        if (!b || !params || !outs) { set_error("NULL argument"); return SCAN_EINVAL; }
+        for (int32_t j = 0; j < b->k; ++j) outs[j] = nullptr;
+        Ctx *c = b->ctx;
+        Graph *g = b->g;
+        SCAN_CUDA(cudaSetDevice(c->device));
+        SCAN_TRY(batch_query_to_device(b, params, mode, (uint8_t *)g->core.ptr, (int32_t *)g->cid.ptr,
+                                       (uint8_t *)g->label.ptr, (int32_t *)g->pairs.ptr, g->nnz,
+                                       (int64_t *)g->npairs.ptr));
+        SCAN_CUDA(cudaMemcpyAsync(g->h_npairs, g->npairs.ptr, 8, cudaMemcpyDeviceToHost, c->stream));
+        SCAN_TRY(take_device_error(g));
+        const int64_t kp = *g->h_npairs, n = g->n;
+        if (kp > b->h_pairs_cap) {
+            if (b->h_pairs) cudaFreeHost(b->h_pairs);
+            b->h_pairs = nullptr;
+            b->h_pairs_cap = 0;
+            SCAN_CUDA(cudaMallocHost(&b->h_pairs, 8 * (size_t)kp + 8));
+            b->h_pairs_cap = kp;
+        }
+        if (n > 0) {
+            SCAN_CUDA(cudaMemcpyAsync(b->h_core, g->core.ptr, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+            SCAN_CUDA(cudaMemcpyAsync(b->h_cid, g->cid.ptr, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+            SCAN_CUDA(cudaMemcpyAsync(b->h_label, g->label.ptr, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (kp > 0)
+            SCAN_CUDA(cudaMemcpyAsync(b->h_pairs, g->pairs.ptr, 8 * (size_t)kp, cudaMemcpyDeviceToHost, c->stream));
+        SCAN_CUDA(cudaStreamSynchronize(c->stream));
+        // split: pairs are sorted by vertex, so each graph owns a contiguous run
+        int64_t pcur = 0;
+        for (int32_t j = 0; j < b->k; ++j) {
+            const int64_t vb = b->vbase[j], ve = b->vbase[j + 1];
+            int64_t pend = pcur;
+            while (pend < kp && b->h_pairs[2 * pend] < ve) ++pend;
+            scan_result *r = result_new((int32_t)(ve - vb), pend - pcur, false);
+            if (!r) {
+                for (int32_t i = 0; i < j; ++i) { scan_result_free(outs[i]); outs[i] = nullptr; }
+                set_error("result allocation failed");
+                return SCAN_ENOMEM;
+            }
+            for (int64_t v = vb; v < ve; ++v) {
+                r->core[v - vb] = b->h_core[v];
+                r->label[v - vb] = b->h_label[v];
+                const int32_t x = b->h_cid[v];
+                r->cid[v - vb] = x >= 0 ? x - (int32_t)vb : -1;
+            }
+            for (int64_t i = pcur; i < pend; ++i) {
+                r->pairs[2 * (i - pcur)] = b->h_pairs[2 * i] - (int32_t)vb;
+                r->pairs[2 * (i - pcur) + 1] = b->h_pairs[2 * i + 1] - (int32_t)vb;
+            }
+            outs[j] = r;
+            pcur = pend;
+        }
+        return SCAN_OK;
+    } catch (...) {
+        set_error("host allocation failed");
+        return SCAN_ENOMEM;
+    }
+}
+
+scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs) {
+    try {
+        if (!gs || !params || !outs || k < 1) { set_error("bad arguments"); return SCAN_EINVAL; }
+        Ctx *c = gs[0]->ctx;
+        for (int32_t j = 0; j < k; ++j)
+            if (!gs[j] || gs[j]->ctx != c) { set_error("all graphs of a batch must share one context"); return SCAN_EINVAL; }
+        SCAN_CUDA(cudaSetDevice(c->device));
+        // bring every graph's CSR back to the host and build the union
+        std::vector<std::vector<int64_t>> offs((size_t)k);
+        std::vector<std::vector<int32_t>> adjs((size_t)k);
+        std::vector<int32_t> ns((size_t)k);
+        std::vector<const int64_t *> po((size_t)k);
+        std::vector<const int32_t *> pa((size_t)k);
+        for (int32_t j = 0; j < k; ++j) {
+            Graph *g = gs[j];
+            ns[j] = g->n;
+            offs[j].resize((size_t)g->n + 1);
+            adjs[j].resize((size_t)std::max<int64_t>(g->nnz, 1));
+            SCAN_CUDA(cudaMemcpyAsync(offs[j].data(), g->off.ptr, 8 * ((size_t)g->n + 1), cudaMemcpyDeviceToHost,
+                                      c->stream));
+            if (g->nnz > 0)
+                SCAN_CUDA(cudaMemcpyAsync(adjs[j].data(), g->adj.ptr, 4 * (size_t)g->nnz, cudaMemcpyDeviceToHost,
+                                          c->stream));
+            po[j] = offs[j].data();
+            pa[j] = adjs[j].data();
+        }
+        SCAN_CUDA(cudaStreamSynchronize(c->stream));
+        scan_batch *b = nullptr;
+        SCAN_TRY(batch_create(c, k, ns.data(), po.data(), pa.data(), &b));
+        scan_status s = scan_batch_query(b, params, SCAN_Q_RECOMPUTE, outs);
+        scan_batch_free(b);
+        return s;
+    } catch (...) {
+        set_error("host allocation failed");
+        return SCAN_ENOMEM;
+    }
+}
+
+}  // extern "C"

@@ -145,14 +145,16 @@ __device__ __forceinline__ int32_t probe_group(const SlotPlan &pl, const int64_t
 template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
 __global__ void __launch_bounds__(256) k_owner_small(
     const int32_t *__restrict__ owners, int32_t nown, const int64_t *__restrict__ off,
-    const int32_t *__restrict__ adj, const int32_t *__restrict__ deg, const uint32_t *__restrict__ rev, uint64_t pp,
-    uint64_t qq, uint8_t *__restrict__ sim, int32_t *__restrict__ cn) {
+    const int32_t *__restrict__ adj, const int32_t *__restrict__ deg, const uint32_t *__restrict__ rev, QParams qp,
+    uint8_t *__restrict__ sim, int32_t *__restrict__ cn) {
     __shared__ int32_t tables[256 / kWarp][kSmallTable];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *t = tables[wid];
     const int warps_total = gridDim.x * (blockDim.x / kWarp);
     for (int32_t i = blockIdx.x * (blockDim.x / kWarp) + wid; i < nown; i += warps_total) {
         const int32_t v = owners[i];
+        uint64_t pp, qq;
+        qp.eps(v, pp, qq);
         const int64_t b = off[v];
         const int32_t dv = (int32_t)(off[v + 1] - b);
         const int logc = max(5, ceil_log2(2 * dv));
@@ -172,16 +174,76 @@ __global__ void __launch_bounds__(256) k_owner_small(
 }
 
 // ------------------------------------------------------------ big owners
-template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
-__global__ void k_owner_cta(const Item *__restrict__ items, const int64_t *__restrict__ off,
-                            const int32_t *__restrict__ adj, const int32_t *__restrict__ deg,
-                            const uint32_t *__restrict__ rev, uint64_t pp, uint64_t qq, uint8_t *__restrict__ sim,
-                            int32_t *__restrict__ cn, int32_t *__restrict__ acc) {
+constexpr int kPiece = 256;  // elements of a long row one warp probes per grab
+constexpr int kUnroll = 8;   // independent loads per lane issued before probing
+
+// First index of row r[0, len) holding a value >= x (bounded binary search).
+__device__ __forceinline__ int32_t row_lower_bound(const int32_t *__restrict__ r, int32_t len, int32_t x) {
+    int32_t lo = 0, hi = len;
+    for (int it = 0; it < 40 && lo < hi; ++it) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(r + mid) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive block-wide prefix sum; every thread gets the total.
+template <int BLOCK, typename T>
+__device__ __forceinline__ T block_scan(T x, T *total, T *wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < BLOCK / 32 ? wsum[lane] : T(0);
+        T si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < BLOCK / 32) wsum[lane] = si - s;
+        if (lane == BLOCK / 32 - 1) wsum[BLOCK / 32] = si;
+    }
+    __syncthreads();
+    const T ex = inc - x + wsum[wid];
+    *total = wsum[BLOCK / 32];
+    __syncthreads();
+    return ex;
+}
+
+// One CTA per work item (owner v, value-chunk of nbr(v), slot range). The
+// item's slots are taken BLOCK at a time ("rounds"): every thread plans one
+// slot, the owned edges that need counting are compacted in shared memory,
+// long rows are cut into kPiece-element pieces that warps grab from a
+// shared counter (so no warp waits on another's row), and short rows are
+// probed one lane each. Every lane issues kUnroll independent loads before
+// it probes, to keep loads in flight.
+template <int BLOCK, bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
+__global__ void __launch_bounds__(BLOCK) k_owner_cta(const Item *__restrict__ items, const int64_t *__restrict__ off,
+                                                     const int32_t *__restrict__ adj, const int32_t *__restrict__ deg,
+                                                     const uint32_t *__restrict__ rev, QParams qp,
+                                                     uint8_t *__restrict__ sim, int32_t *__restrict__ cn,
+                                                     int32_t *__restrict__ acc) {
     extern __shared__ int32_t t[];
+    __shared__ int32_t w_rel[BLOCK], w_u[BLOCK], w_du[BLOCK], w_start[BLOCK], w_len[BLOCK], w_cnt[BLOCK];
+    __shared__ int32_t l_idx[BLOCK], l_poff[BLOCK + 1], s_idx[BLOCK];
+    __shared__ long long wsum64[BLOCK / 32 + 1];
+    __shared__ int32_t wsum32[BLOCK / 32 + 1];
+    __shared__ int32_t piece_ctr, short_ctr;
+
     const Item it = items[blockIdx.x];
     const int32_t v = it.v;
     const int64_t b = off[v];
     const int32_t dv = (int32_t)(off[v + 1] - b);
+    uint64_t pp, qq;
+    qp.eps(v, pp, qq);
     const int32_t *rv = adj + b;
     const int32_t tb = it.chunk * kChunk;
     const int32_t te = min(tb + kChunk, dv);
@@ -190,23 +252,139 @@ __global__ void k_owner_cta(const Item *__restrict__ items, const int64_t *__res
     const int32_t hi = te == dv ? INT32_MAX : rv[te];
     const int logc = max(5, ceil_log2(2 * (te - tb)));
     const int cap = 1 << logc;
-    for (int k = threadIdx.x; k < cap; k += blockDim.x) t[k] = kEmpty;
+    for (int k = threadIdx.x; k < cap; k += BLOCK) t[k] = kEmpty;
     __syncthreads();
-    for (int k = tb + threadIdx.x; k < te; k += blockDim.x) table_insert(t, logc, rv[k]);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int32_t g0 = it.sb + wid * kWarp; g0 < it.se; g0 += nw * kWarp) {
-        const int64_t s = b + g0 + lane;
-        const SlotPlan pl =
-            plan_slot<PRUNE>(s, g0 + lane < it.se, v, dv, adj, deg, rev, pp, qq, sim, it.chunk == 0);
-        int32_t c;
-        if (chunked) {
-            c = probe_group<true>(pl, off, adj, t, logc, lo, hi);
-            if (pl.work && c) atomicAdd(acc + s, c);
-        } else {
-            c = probe_group<false>(pl, off, adj, t, logc, lo, hi);
-            if (pl.work) emit<WRITE_SIM, WRITE_CN>(s, c + 2, pl.du, dv, rev, pp, qq, sim, cn);
+    for (int k = tb + threadIdx.x; k < te; k += BLOCK) table_insert(t, logc, rv[k]);
+    const int lane = threadIdx.x & 31;
+
+    for (int32_t r0 = it.sb; r0 < it.se; r0 += BLOCK) {
+        // ---- plan one slot per thread
+        const int32_t rel = r0 + threadIdx.x;
+        bool work = false;
+        int32_t u = -1, du = 0, start = 0, len = 0;
+        if (rel < it.se) {
+            const int64_t s = b + rel;
+            u = adj[s];
+            du = deg[u];
+            if (dev::rank_less(du, u, dv, v)) {
+                work = true;
+                if (PRUNE) {
+                    if (dev::prune_dissimilar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) {
+                        work = false;
+                    } else if (dev::prune_similar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) {
+                        if (it.chunk == 0) { sim[s] = 1; sim[rev[s]] = 1; }
+                        work = false;
+                    }
+                }
+                if (work) {
+                    len = du;
+                    if (chunked) {
+                        const int32_t *ru = adj + off[u];
+                        start = lo == INT32_MIN ? 0 : row_lower_bound(ru, du, lo);
+                        const int32_t end = hi == INT32_MAX ? du : row_lower_bound(ru, du, hi);
+                        len = end - start;
+                    }
+                }
+            }
         }
+        const bool is_long = work && len >= kWarp;
+        const bool is_short = work && len > 0 && len < kWarp;
+        // packed counts: work | long << 21 | short << 42
+        const long long flags = (long long)work | ((long long)is_long << 21) | ((long long)is_short << 42);
+        long long tot;
+        const long long ex = block_scan<BLOCK, long long>(flags, &tot, wsum64);
+        const int32_t npieces_mine = is_long ? (len + kPiece - 1) / kPiece : 0;
+        int32_t tot_pieces;
+        const int32_t pex = block_scan<BLOCK, int32_t>(npieces_mine, &tot_pieces, wsum32);
+        const int32_t n_work = (int32_t)(tot & 0x1FFFFF);
+        const int32_t n_long = (int32_t)((tot >> 21) & 0x1FFFFF);
+        const int32_t n_short = (int32_t)((tot >> 42) & 0x1FFFFF);
+        if (work) {
+            const int32_t e = (int32_t)(ex & 0x1FFFFF);
+            w_rel[e] = rel;
+            w_u[e] = u;
+            w_du[e] = du;
+            w_start[e] = start;
+            w_len[e] = len;
+            w_cnt[e] = 0;
+            if (is_long) {
+                const int32_t l = (int32_t)((ex >> 21) & 0x1FFFFF);
+                l_idx[l] = e;
+                l_poff[l] = pex;
+            }
+            if (is_short) s_idx[(ex >> 42) & 0x1FFFFF] = e;
+        }
+        if (threadIdx.x == 0) {
+            l_poff[n_long] = tot_pieces;
+            piece_ctr = 0;
+            short_ctr = 0;
+        }
+        __syncthreads();
+
+        // ---- long rows: warps grab pieces
+        for (int guard = 0; guard < (1 << 30); ++guard) {
+            int32_t p = 0;
+            if (lane == 0) p = atomicAdd(&piece_ctr, 1);
+            p = __shfl_sync(0xffffffffu, p, 0);
+            if (p >= tot_pieces) break;
+            int32_t lo_i = 0, hi_i = n_long;  // last l with l_poff[l] <= p
+            while (hi_i - lo_i > 1) {
+                const int32_t mid = (lo_i + hi_i) >> 1;
+                if (l_poff[mid] <= p) lo_i = mid;
+                else hi_i = mid;
+            }
+            const int32_t e = l_idx[lo_i];
+            const int32_t o = (p - l_poff[lo_i]) * kPiece;
+            const int32_t plen = min(kPiece, w_len[e] - o);
+            const int32_t *src_row = adj + off[w_u[e]] + w_start[e] + o;
+            int32_t x[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) {
+                const int k = lane + j * kWarp;
+                x[j] = k < plen ? __ldg(src_row + k) : 0;
+            }
+            int c = 0;
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j)
+                if (lane + j * kWarp < plen) c += table_has(t, logc, x[j]);
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (lane == 0 && c) atomicAdd(&w_cnt[e], c);
+        }
+        // ---- short rows: one lane each, 32 per grab
+        for (int guard = 0; guard < (1 << 30); ++guard) {
+            int32_t q = 0;
+            if (lane == 0) q = atomicAdd(&short_ctr, kWarp);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q >= n_short) break;
+            const int32_t k = q + lane;
+            if (k < n_short) {
+                const int32_t e = s_idx[k];
+                const int32_t *src_row = adj + off[w_u[e]] + w_start[e];
+                const int32_t L = w_len[e];
+                int c = 0;
+                for (int32_t j0 = 0; j0 < L; j0 += kUnroll) {
+                    int32_t x[kUnroll];
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) x[j] = j0 + j < L ? __ldg(src_row + j0 + j) : 0;
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j)
+                        if (j0 + j < L) c += table_has(t, logc, x[j]);
+                }
+                w_cnt[e] = c;
+            }
+        }
+        __syncthreads();
+        // ---- emit one owned edge per thread
+        if (threadIdx.x < n_work) {
+            const int32_t e = threadIdx.x;
+            const int64_t s = b + w_rel[e];
+            if (chunked) {
+                if (w_cnt[e]) atomicAdd(acc + s, w_cnt[e]);
+            } else {
+                emit<WRITE_SIM, WRITE_CN>(s, w_cnt[e] + 2, w_du[e], dv, rev, pp, qq, sim, cn);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -215,11 +393,13 @@ template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
 __global__ void __launch_bounds__(256) k_owner_finish(const int32_t *__restrict__ owners, int32_t nown,
                                                       const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                                       const int32_t *__restrict__ deg, const uint32_t *__restrict__ rev,
-                                                      uint64_t pp, uint64_t qq, uint8_t *__restrict__ sim,
+                                                      QParams qp, uint8_t *__restrict__ sim,
                                                       int32_t *__restrict__ cn, int32_t *__restrict__ acc) {
     const int32_t v = owners[blockIdx.x];
     const int64_t b = off[v];
     const int32_t dv = (int32_t)(off[v + 1] - b);
+    uint64_t pp, qq;
+    qp.eps(v, pp, qq);
     for (int32_t k = threadIdx.x; k < dv; k += blockDim.x) {
         const int64_t s = b + k;
         const int32_t u = adj[s], du = deg[u];
@@ -300,7 +480,6 @@ __global__ void k_sched_write(const int32_t *__restrict__ deg, int32_t n, const 
 
 // Class table sizes (ints) and block sizes.
 static const int kClassCap[4] = {0, 2048, 16384, 2 * kChunk};
-static const int kClassBlock[4] = {0, 128, 256, 512};
 
 scan_status owner_schedule_build(Graph *g) {
     Ctx *c = g->ctx;
@@ -344,7 +523,7 @@ scan_status owner_schedule_build(Graph *g) {
 }
 
 template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
-static scan_status launch_owner_t(Graph *g, uint64_t pp, uint64_t qq, int32_t *cn) {
+static scan_status launch_owner_t(Graph *g, const QParams &qp, int32_t *cn) {
     Ctx *c = g->ctx;
     auto *off = (const int64_t *)g->off.ptr;
     auto *adj = (const int32_t *)g->adj.ptr;
@@ -357,33 +536,41 @@ static scan_status launch_owner_t(Graph *g, uint64_t pp, uint64_t qq, int32_t *c
         const int64_t ni = g->n_items[cls];
         if (ni == 0) continue;
         const size_t smem = sizeof(int32_t) * (size_t)kClassCap[cls];
-        auto kern = k_owner_cta<PRUNE, WRITE_SIM, WRITE_CN>;
-        if (smem > 48 * 1024) SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)ni, kClassBlock[cls], smem, c->stream>>>((const Item *)g->items[cls].ptr, off, adj, deg, rev,
-                                                                   pp, qq, sim, cn, acc);
+        const Item *items = (const Item *)g->items[cls].ptr;
+        if (cls == 3) {
+            auto kern = k_owner_cta<1024, PRUNE, WRITE_SIM, WRITE_CN>;
+            SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<(unsigned)ni, 1024, smem, c->stream>>>(items, off, adj, deg, rev, qp, sim, cn, acc);
+        } else if (cls == 2) {
+            auto kern = k_owner_cta<512, PRUNE, WRITE_SIM, WRITE_CN>;
+            SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<(unsigned)ni, 512, smem, c->stream>>>(items, off, adj, deg, rev, qp, sim, cn, acc);
+        } else {
+            k_owner_cta<256, PRUNE, WRITE_SIM, WRITE_CN><<<(unsigned)ni, 256, smem, c->stream>>>(
+                items, off, adj, deg, rev, qp, sim, cn, acc);
+        }
         c->launches++;
     }
     if (g->n_small > 0) {
         k_owner_small<PRUNE, WRITE_SIM, WRITE_CN><<<grid_for((int64_t)g->n_small * kWarp, 256, c->num_sms * 16), 256, 0,
                                                     c->stream>>>((const int32_t *)g->owners_small.ptr, g->n_small, off,
-                                                                 adj, deg, rev, pp, qq, sim, cn);
+                                                                 adj, deg, rev, qp, sim, cn);
         c->launches++;
     }
     if (g->n_chunked > 0) {
         k_owner_finish<PRUNE, WRITE_SIM, WRITE_CN><<<(unsigned)g->n_chunked, 256, 0, c->stream>>>(
-            (const int32_t *)g->owners_chunked.ptr, g->n_chunked, off, adj, deg, rev, pp, qq, sim, cn, acc);
+            (const int32_t *)g->owners_chunked.ptr, g->n_chunked, off, adj, deg, rev, qp, sim, cn, acc);
         c->launches++;
     }
     SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;
 }
 
-scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, uint64_t pp, uint64_t qq,
-                               int32_t *cn) {
+scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn) {
     if (g->m == 0) return SCAN_OK;
-    if (prune) return launch_owner_t<true, true, false>(g, pp, qq, cn);
-    if (write_cn && !write_sim) return launch_owner_t<false, false, true>(g, pp, qq, cn);
-    return launch_owner_t<false, true, false>(g, pp, qq, cn);
+    if (prune) return launch_owner_t<true, true, false>(g, qp, cn);
+    if (write_cn && !write_sim) return launch_owner_t<false, false, true>(g, qp, cn);
+    return launch_owner_t<false, true, false>(g, qp, cn);
 }
 
 }  // namespace scan

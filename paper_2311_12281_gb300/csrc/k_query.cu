@@ -40,13 +40,15 @@ template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
 __global__ void __launch_bounds__(kBlock) k_isect_bsearch(
     const int64_t *__restrict__ off, const int32_t *__restrict__ adj, const int32_t *__restrict__ src,
     const uint32_t *__restrict__ rev, const int32_t *__restrict__ deg, const uint32_t *__restrict__ oe, int64_t m,
-    uint64_t pp, uint64_t qq, uint8_t *__restrict__ sim, int32_t *__restrict__ cn) {
+    QParams qp, uint8_t *__restrict__ sim, int32_t *__restrict__ cn) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (kBlock / kWarp);
     for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp; i < m; i += warps) {
         const uint32_t e = oe[i];
         const int32_t u = src[e], v = adj[e];
         const int32_t du = deg[u], dv = deg[v];
+        uint64_t pp, qq;
+        qp.eps(u, pp, qq);
         if (PRUNE) {
             if (dev::prune_dissimilar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) continue;
             if (dev::prune_similar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) {
@@ -73,10 +75,12 @@ __global__ void __launch_bounds__(kBlock) k_isect_bsearch(
 __global__ void __launch_bounds__(kBlock) k_sim_from_counts(
     const int32_t *__restrict__ adj, const int32_t *__restrict__ src, const uint32_t *__restrict__ rev,
     const int32_t *__restrict__ deg, const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ cn,
-    uint64_t pp, uint64_t qq, uint8_t *__restrict__ sim) {
+    QParams qp, uint8_t *__restrict__ sim) {
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
         const uint32_t e = oe[i];
         const int32_t u = src[e], v = adj[e];
+        uint64_t pp, qq;
+        qp.eps(u, pp, qq);
         if (dev::eps_similar((uint64_t)cn[e], (uint64_t)deg[u] + 1, (uint64_t)deg[v] + 1, pp, qq)) {
             sim[e] = 1;
             sim[rev[e]] = 1;
@@ -87,10 +91,11 @@ __global__ void __launch_bounds__(kBlock) k_sim_from_counts(
 // ------------------------------------------------------------------ cores
 // Warp per vertex: count similar slots, stop once 1 + count >= mu.
 __global__ void __launch_bounds__(kBlock) k_core(const int64_t *__restrict__ off, const uint8_t *__restrict__ sim,
-                                                 int32_t n, uint32_t mu, uint8_t *__restrict__ core) {
+                                                 int32_t n, QParams qp, uint8_t *__restrict__ core) {
     const int64_t u = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;
     const int lane = threadIdx.x & 31;
     if (u >= n) return;
+    const uint32_t mu = qp.mu_of((int32_t)u);
     const int64_t b = off[u], e = off[u + 1];
     uint32_t cnt = 1;  // u itself: sigma(u, u) = 1
     for (int64_t s0 = b; s0 < e && cnt < mu; s0 += kWarp) {
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kBlock) k_label(const int64_t *__restrict__ of
 
 }  // namespace
 
-static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write_cn, uint64_t pp, uint64_t qq,
+static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp,
                                 int32_t *cn) {
     Ctx *c = g->ctx;
     if (g->m == 0) return SCAN_OK;
@@ -287,11 +292,11 @@ static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write
     auto *oe = (const uint32_t *)g->oe.ptr;
     auto *sim = (uint8_t *)g->sim.ptr;
     if (prune)
-        k_isect_bsearch<true, true, false><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, pp, qq, sim, cn);
+        k_isect_bsearch<true, true, false><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, qp, sim, cn);
     else if (write_cn && !write_sim)
-        k_isect_bsearch<false, false, true><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, pp, qq, sim, cn);
+        k_isect_bsearch<false, false, true><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, qp, sim, cn);
     else
-        k_isect_bsearch<false, true, false><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, pp, qq, sim, cn);
+        k_isect_bsearch<false, true, false><<<grid, kBlock, 0, c->stream>>>(off, adj, src, rev, deg, oe, g->m, qp, sim, cn);
     c->launches++;
     SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;
@@ -300,18 +305,17 @@ static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write
 scan_status build_count_cache(Graph *g) {
     Ctx *c = g->ctx;
     if (!g->cn_cache.ptr) SCAN_TRY(dev_alloc(c, g->cn_cache, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
-    SCAN_TRY(launch_owner_isect(g, false, false, true, 0, 0, (int32_t *)g->cn_cache.ptr));
+    SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, (int32_t *)g->cn_cache.ptr));
     g->cache_valid = true;
     return SCAN_OK;
 }
 
-scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_t *core, int32_t *cid,
+scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *core, int32_t *cid,
                            uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs) {
     Ctx *c = g->ctx;
     cudaStream_t st = c->stream;
     const int32_t n = g->n;
     const int64_t nnz = g->nnz, m = g->m;
-    const uint64_t pp = (uint64_t)p.eps_num * p.eps_num, qq = (uint64_t)p.eps_den * p.eps_den;
     auto *off = (const int64_t *)g->off.ptr;
     auto *adj = (const int32_t *)g->adj.ptr;
     auto *src = (const int32_t *)g->src.ptr;
@@ -329,13 +333,13 @@ scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_
         if (use_cache) {
             if (m > 0) {
                 k_sim_from_counts<<<grid_for(m, kBlock, c->num_sms * 32), kBlock, 0, st>>>(
-                    adj, src, rev, deg, oe, m, (const int32_t *)g->cn_cache.ptr, pp, qq, sim);
+                    adj, src, rev, deg, oe, m, (const int32_t *)g->cn_cache.ptr, qp, sim);
                 c->launches++;
             }
         } else if (mode & SCAN_Q_PLAIN) {
-            SCAN_TRY(launch_isect(g, false, true, false, pp, qq, nullptr));
+            SCAN_TRY(launch_isect(g, false, true, false, qp, nullptr));
         } else {
-            SCAN_TRY(launch_owner_isect(g, true, true, false, pp, qq, nullptr));
+            SCAN_TRY(launch_owner_isect(g, true, true, false, qp, nullptr));
         }
     }
 
@@ -348,7 +352,7 @@ scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_
     const unsigned gt = grid_for(n, kBlock);
     {
         StageTimer t(c, SCAN_STAGE_CORE);
-        k_core<<<gw, kBlock, 0, st>>>(off, sim, n, p.mu, core);
+        k_core<<<gw, kBlock, 0, st>>>(off, sim, n, qp, core);
         c->launches++;
     }
     {

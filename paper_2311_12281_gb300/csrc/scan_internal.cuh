@@ -79,6 +79,29 @@ struct Graph {
     }
 };
 
+// Query parameters seen by the kernels: either one (eps, mu) for the whole
+// graph, or -- for a batch of graphs stored as one disjoint union -- a graph
+// index per vertex and per-graph parameter arrays in device memory.
+struct QParams {
+    uint64_t pp = 0, qq = 0;        // eps_num^2, eps_den^2
+    uint32_t mu = 0;
+    const int32_t *gid = nullptr;   // [n] graph index of every vertex, or null
+    const uint64_t *gpp = nullptr;  // [k] per-graph eps_num^2
+    const uint64_t *gqq = nullptr;  // [k] per-graph eps_den^2
+    const uint32_t *gmu = nullptr;  // [k] per-graph mu
+    __device__ __forceinline__ void eps(int32_t v, uint64_t &p2, uint64_t &q2) const {
+        if (gid) {
+            const int32_t g = gid[v];
+            p2 = gpp[g];
+            q2 = gqq[g];
+        } else {
+            p2 = pp;
+            q2 = qq;
+        }
+    }
+    __device__ __forceinline__ uint32_t mu_of(int32_t v) const { return gid ? gmu[gid[v]] : mu; }
+};
+
 struct StageMark {
     int stage;
     cudaEvent_t start, stop;
@@ -119,11 +142,36 @@ struct StageTimer {
     }
 };
 
+}  // namespace scan
+
+// The opaque ABI handles are the internal objects.
+struct scan_ctx : scan::Ctx {};
+struct scan_graph : scan::Graph {};
+
+// Host result of one query (library-owned until scan_result_free).
+struct scan_result {
+    int32_t n = 0;
+    int64_t k = 0;
+    uint8_t *core = nullptr;
+    int32_t *cid = nullptr;
+    uint8_t *label = nullptr;
+    int32_t *pairs = nullptr;
+    bool pinned = false;  // arrays from cudaMallocHost (else malloc)
+};
+
+namespace scan {
+
 // ---- host helpers (abi.cu)
 void set_error(const std::string &msg);
 scan_status cuda_fail(cudaError_t e, const char *what);
 scan_status dev_alloc(Ctx *c, DevBuf &b, size_t bytes);
 void dev_free(Ctx *c, DevBuf &b);
+scan_status check_params(const scan_params *p);
+scan_status take_device_error(Graph *g);
+scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, bool on_dev,
+                         Graph **out);
+void graph_destroy(Graph *g);
+scan_result *result_new(int32_t n, int64_t k, bool pinned);
 
 #define SCAN_CUDA(call)                                              \
     do {                                                             \
@@ -141,12 +189,19 @@ void dev_free(Ctx *c, DevBuf &b);
 scan_status launch_exclusive_scan_i32_to_i64(Ctx *c, const int32_t *in, int64_t *out, int64_t count,
                                              DevBuf &tmp);
 scan_status graph_prepare(Graph *g);                    // deg, src, rev, validation, oe
-scan_status query_pipeline(Graph *g, const scan_params &p, uint32_t mode, uint8_t *core, int32_t *cid,
+scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *core, int32_t *cid,
                            uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs);
 scan_status build_count_cache(Graph *g);
 scan_status owner_schedule_build(Graph *g);
-scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, uint64_t pp, uint64_t qq,
-                               int32_t *cn);
+scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);
+
+inline QParams uniform_params(const scan_params &p) {
+    QParams q;
+    q.pp = (uint64_t)p.eps_num * p.eps_num;
+    q.qq = (uint64_t)p.eps_den * p.eps_den;
+    q.mu = p.mu;
+    return q;
+}
 
 inline unsigned grid_for(int64_t items, int per_block, int max_blocks = 1 << 30) {
     int64_t b = (items + per_block - 1) / per_block;
