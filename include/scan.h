@@ -220,6 +220,34 @@ SCAN_API void scan_batch_free(scan_batch *b);
  * temporary union, answers all k queries (full recompute) and frees it. */
 SCAN_API scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs);
 
+/* ----------------------------------------------- no-allocation counting */
+/*
+ * Closed common counts |N[u] cap N[v]| for every slot of a caller's device
+ * CSR, with no memory allocation of any kind. The paper has no counterpart;
+ * this exists for callers that cannot allocate device memory -- code that
+ * runs inside another framework's memory pool or under a hard memory budget,
+ * or at a point where a cudaMalloc/cudaFree (which can synchronise the whole
+ * device) is not allowed.
+ *
+ * offsets int64[n+1], adj int32[nnz] and cn int32[nnz] are device pointers
+ * owned by the caller; the CSR must meet scan_graph_load's contract (checked;
+ * SCAN_EINVAL names the first bad slot). cn[s] receives the count of the
+ * slot s, as scan_graph_copy_counts would return it. Runs on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) on the current device and
+ * returns when the counts are written (it synchronises that stream).
+ *
+ * Working memory is one fixed 64 MiB __device__ array inside the library
+ * (held by every GPU that loads it until the process exits): graphs need
+ * 4(n+1) + 8 nnz bytes plus alignment of it, about n + 2 nnz <= 16.7M
+ * entries; larger graphs get SCAN_EINVAL before any device work. The first
+ * call on a device looks up that array's device address (once per device);
+ * make that first call before any stream capture. All calls share the one
+ * array and it keeps the last call's contents, so calls that overlap on the
+ * GPU (other threads, other streams) race: serialise them.
+ */
+SCAN_API scan_status scan_common_counts_static(const int64_t *offsets, const int32_t *adj, int32_t n, int64_t nnz,
+                                               int32_t *cn, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

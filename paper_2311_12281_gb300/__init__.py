@@ -81,6 +81,7 @@ SIGNATURES = {
     "scan_batch_query_device": (ctypes.c_int, [_VP, _VP, _U32, ctypes.POINTER(scan_device_out)]),
     "scan_batch_free": (None, [_VP]),
     "scan_query_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
+    "scan_common_counts_static": (ctypes.c_int, [_VP, _VP, _I32, _I64, _VP, _VP]),
     "scan_result_n": (_I32, [_VP]),
     "scan_result_core": (_VP, [_VP]),
     "scan_result_cluster": (_VP, [_VP]),
@@ -301,6 +302,13 @@ def scan_query_batch(graphs, params) -> list:
     outs = (ctypes.c_void_p * k)()
     _check(lib().scan_query_batch(gs, _params_array(params), k, outs))
     return [_result_to_numpy(outs[j]) for j in range(k)]
+
+
+def scan_common_counts_static(offsets: int, adj: int, n: int, nnz: int, cn: int, stream: int | None = None):
+    """Per-slot closed common counts into the caller's device array `cn`,
+    allocating nothing (all arguments are device addresses). For callers that
+    cannot allocate device memory; see include/scan.h for the size limit."""
+    _check(lib().scan_common_counts_static(offsets, adj, int(n), int(nnz), cn, stream))
 
 
 # --------------------------------------------------------------- convenience
