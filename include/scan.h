@@ -146,6 +146,20 @@ typedef struct scan_params {
     uint32_t mu;      /* mu >= 2 (Definition Core) */
 } scan_params;
 
+/* Kernel family of the similarity stage (common counts). Every family gives
+ * the same result; they differ in speed by graph shape. */
+#define SCAN_STRATEGY_FORWARD 0 /* degree-oriented triangle enumeration: each triangle found once at its
+                                   middle vertex through a shared-memory table (the default) */
+#define SCAN_STRATEGY_OWNER 1   /* per edge: the higher-degree endpoint's row in a shared-memory hash,
+                                   the lower one streamed; skips edges the degrees decide */
+#define SCAN_STRATEGY_BSEARCH 2 /* per edge: binary search of the smaller row in the larger (checkSim
+                                   of Algorithm 2); skips edges the degrees decide */
+/* Select the similarity kernel family used by SCAN_Q_RECOMPUTE and
+ * SCAN_Q_BUILD_CACHE on this graph (SCAN_Q_PLAIN always uses BSEARCH without
+ * pruning). SCAN_EINVAL for an unknown value. */
+SCAN_API scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy);
+SCAN_API int32_t scan_graph_strategy(const scan_graph *g);
+
 /* Query modes. */
 #define SCAN_Q_AUTO 0x0u        /* use the count cache if present, else full recompute */
 #define SCAN_Q_RECOMPUTE 0x1u   /* full recompute with degree pruning; ignore any cache */
@@ -219,6 +233,62 @@ SCAN_API void scan_batch_free(scan_batch *b);
 /* One-call form over graphs loaded separately in one context: builds a
  * temporary union, answers all k queries (full recompute) and frees it. */
 SCAN_API scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs);
+
+/* ------------------------------------------------------------- serving */
+/*
+ * A query server over many resident graphs with continuous batching. Not in
+ * the paper (it clusters one graph per run); its cached counts are the
+ * numerators of Eq. 1 kept per edge across queries.
+ *
+ * Graphs are registered once (the server keeps a pinned host copy) and kept
+ * on the device while memory allows. The first query on a graph computes
+ * and keeps every edge's closed common count; later queries on it skip the
+ * intersection. One worker thread owns the GPU: requests queue as they
+ * arrive and are admitted into max_inflight slots (each with its own CUDA
+ * stream) as slots and device memory free up, so queries on different
+ * graphs overlap on the device; queries on one graph run one at a time.
+ * Admission is by the context's device budget: idle graphs' count caches are
+ * evicted first (least recently used), then idle graphs, which reload from
+ * their host copy when next asked for. A request that can never fit fails
+ * with SCAN_EBUSY. Every result equals the single-query result.
+ *
+ * While a server lives it owns its context: make no other calls on that
+ * context or its graphs. submit / wait / poll / stats are thread-safe.
+ */
+typedef struct scan_server scan_server;
+typedef struct scan_server_opts {
+    int32_t max_inflight; /* concurrent requests on the device, 1..256 */
+    int32_t use_cache;    /* 1: keep per-edge counts after a graph's first query; 0: recompute every query */
+} scan_server_opts;
+typedef struct scan_server_report {
+    uint64_t completed, rejected;
+    double p50_ms, p99_ms, mean_ms; /* latency = completion - submission (queueing included) */
+    double throughput_rps;          /* completed / (last completion - first submission) */
+    uint64_t cache_builds, cache_evictions, graph_loads, graph_evictions;
+    int32_t max_inflight;           /* most requests seen in flight at once */
+    uint64_t device_bytes;          /* context bytes in use */
+} scan_server_report;
+
+SCAN_API scan_status scan_server_create(scan_ctx *ctx, const scan_server_opts *opts, scan_server **out);
+/* Register a host CSR (copied; same contract as scan_graph_load, validated
+ * on its first load). Only while the server is idle; returns its id. */
+SCAN_API scan_status scan_server_add_graph(scan_server *srv, int32_t n, const int64_t *offsets, const int32_t *adj,
+                                           int64_t nnz, int32_t *graph_id);
+/* Queue one query; returns at once with a ticket. SCAN_EINVAL for bad
+ * parameters or an unknown graph id. */
+SCAN_API scan_status scan_server_submit(scan_server *srv, int32_t graph_id, const scan_params *params,
+                                        uint64_t *ticket);
+/* Block until the ticket's query finishes; its status is returned and, on
+ * success, its result (free with scan_result_free). latency_ms may be NULL.
+ * Each ticket can be taken once. */
+SCAN_API scan_status scan_server_wait(scan_server *srv, uint64_t ticket, scan_result **out, double *latency_ms);
+/* Non-blocking: *ready = 0 if still running, else as scan_server_wait. */
+SCAN_API scan_status scan_server_poll(scan_server *srv, uint64_t ticket, scan_result **out, double *latency_ms,
+                                      int32_t *ready);
+SCAN_API scan_status scan_server_stats(scan_server *srv, scan_server_report *stats);
+SCAN_API scan_status scan_server_reset_stats(scan_server *srv);
+/* Finishes queued and running requests, then frees everything it holds. */
+SCAN_API void scan_server_destroy(scan_server *srv);
 
 /* ----------------------------------------------- no-allocation counting */
 /*

@@ -71,6 +71,8 @@ SIGNATURES = {
     "scan_graph_drop_cache": (ctypes.c_int, [_VP]),
     "scan_graph_has_cache": (_I32, [_VP]),
     "scan_graph_copy_counts": (ctypes.c_int, [_VP, _VP]),
+    "scan_graph_set_strategy": (ctypes.c_int, [_VP, _I32]),
+    "scan_graph_strategy": (_I32, [_VP]),
     "scan_query": (ctypes.c_int, [_VP, _U32, _U32, _U32, _PP]),
     "scan_query_ex": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, _PP]),
     "scan_query_device": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, ctypes.POINTER(scan_device_out)]),
@@ -197,6 +199,17 @@ def scan_graph_drop_cache(g: int):
 
 def scan_graph_has_cache(g: int) -> bool:
     return bool(lib().scan_graph_has_cache(g))
+
+
+SCAN_STRATEGY_FORWARD, SCAN_STRATEGY_OWNER, SCAN_STRATEGY_BSEARCH = 0, 1, 2
+
+
+def scan_graph_set_strategy(g: int, strategy: int):
+    _check(lib().scan_graph_set_strategy(g, int(strategy)))
+
+
+def scan_graph_strategy(g: int) -> int:
+    return int(lib().scan_graph_strategy(g))
 
 
 def scan_graph_copy_counts(g: int, nnz: int) -> np.ndarray:
@@ -359,6 +372,9 @@ class Graph:
 
     def drop_cache(self):
         scan_graph_drop_cache(self.handle)
+
+    def set_strategy(self, strategy: int):
+        scan_graph_set_strategy(self.handle, strategy)
 
     def counts(self) -> np.ndarray:
         return scan_graph_copy_counts(self.handle, int(lib().scan_graph_nnz(self.handle)))

@@ -336,6 +336,18 @@ scan_status scan_graph_drop_cache(scan_graph *g) {
 
 int32_t scan_graph_has_cache(const scan_graph *g) { return g && g->cache_valid ? 1 : 0; }
 
+scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy) {
+    if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
+    if (strategy != SCAN_STRATEGY_FORWARD && strategy != SCAN_STRATEGY_OWNER && strategy != SCAN_STRATEGY_BSEARCH) {
+        set_error("unknown strategy " + std::to_string(strategy));
+        return SCAN_EINVAL;
+    }
+    g->strategy = strategy;
+    return SCAN_OK;
+}
+
+int32_t scan_graph_strategy(const scan_graph *g) { return g ? g->strategy : -1; }
+
 scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out) {
     if (!g || !out) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
     if (!g->cache_valid) { set_error("graph has no common-count cache"); return SCAN_EINVAL; }

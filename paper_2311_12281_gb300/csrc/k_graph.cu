@@ -148,9 +148,10 @@ scan_status graph_prepare(Graph *g) {
     }
     dev_free(c, badb);
 
-    // degree-oriented edge list
+    // degree-oriented edge list, grouped by the lower endpoint (offsets kept in foff)
     int32_t *cnt = (int32_t *)g->cnt.ptr;
-    int64_t *pos = (int64_t *)g->cnt_off.ptr;
+    SCAN_TRY(dev_alloc(c, g->foff, 8 * ((size_t)n + 1)));
+    int64_t *pos = (int64_t *)g->foff.ptr;
     if (n > 0) {
         k_count_oriented<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(off, adj, deg, n, cnt);
         c->launches++;

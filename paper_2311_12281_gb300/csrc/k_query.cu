@@ -305,7 +305,10 @@ static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write
 scan_status build_count_cache(Graph *g) {
     Ctx *c = g->ctx;
     if (!g->cn_cache.ptr) SCAN_TRY(dev_alloc(c, g->cn_cache, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
-    SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, (int32_t *)g->cn_cache.ptr));
+    int32_t *cn = (int32_t *)g->cn_cache.ptr;
+    if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, cn));
+    else if (g->strategy == SCAN_STRATEGY_BSEARCH) SCAN_TRY(launch_isect(g, false, false, true, QParams{}, cn));
+    else SCAN_TRY(launch_fwd_counts(g, false, true, QParams{}, cn));
     g->cache_valid = true;
     return SCAN_OK;
 }
@@ -338,8 +341,12 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
             }
         } else if (mode & SCAN_Q_PLAIN) {
             SCAN_TRY(launch_isect(g, false, true, false, qp, nullptr));
-        } else {
+        } else if (g->strategy == SCAN_STRATEGY_OWNER) {
             SCAN_TRY(launch_owner_isect(g, true, true, false, qp, nullptr));
+        } else if (g->strategy == SCAN_STRATEGY_BSEARCH) {
+            SCAN_TRY(launch_isect(g, true, true, false, qp, nullptr));
+        } else {
+            SCAN_TRY(launch_fwd_counts(g, true, false, qp, nullptr));
         }
     }
 

@@ -56,6 +56,17 @@ struct Graph {
     DevBuf owners_chunked;  // int32[n_chunked] owners whose row is split in value chunks
     int32_t n_chunked = 0;
     DevBuf acc;             // int32[nnz] partial counts of chunked owners (kept zero between queries)
+    // degree-oriented (forward) lists for triangle-based counting
+    DevBuf foff;            // int64[n+1] offsets of out(x) in oe / fadj (built at load)
+    DevBuf fadj;            // int32[m] out(x) neighbour ids, ascending
+    DevBuf fin;             // uint32[nnz] for a slot (b, a) with a below b: index of a->b in fadj
+    DevBuf fcnt;            // int32[m] triangle counts per oriented edge
+    DevBuf fwd_owners;      // warp-level owners
+    DevBuf fwd_items[3];    // CTA items, by table class 1..2
+    int64_t fwd_items_n[3] = {0, 0, 0};
+    int32_t fwd_small = 0;
+    bool fwd_ready = false;
+    int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
     // per-query scratch
     DevBuf sim;             // uint8[nnz] 1 = eps-similar
     DevBuf core, cid, parent, label;
@@ -73,7 +84,8 @@ struct Graph {
     template <class F>
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
-                          &items[2], &items[3], &owners_chunked, &acc, &sim, &core, &cid, &parent, &label,
+                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
+                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &sim, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
         for (DevBuf *b : bufs) f(*b);
     }
@@ -194,6 +206,8 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
 scan_status build_count_cache(Graph *g);
 scan_status owner_schedule_build(Graph *g);
 scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);
+scan_status fwd_prepare(Graph *g);
+scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);
 
 inline QParams uniform_params(const scan_params &p) {
     QParams q;

@@ -134,6 +134,38 @@ def test_rmat_scale14_full_sweep(ps, ctx):
     check_graph(ps, ctx, g, params)
 
 
+@pytest.mark.parametrize("which", ["fig1", "rmat14", "chung_lu", "star", "union"])
+def test_every_strategy_gives_the_oracle_result(ps, ctx, which):
+    if which == "fig1":
+        gd = load_golden("fig1.txt")
+        e = list(map(int, gd["edges"][0].split()))
+        g = gg.from_edges(int(gd["n"][0]), list(zip(e[0::2], e[1::2])))
+    elif which == "rmat14":
+        g = gg.rmat_s14()
+    elif which == "chung_lu":
+        g = gg.chung_lu(9001, 40.0, 2.1, seed=31)
+    elif which == "star":
+        g = gg.from_edges(5000, [(0, i) for i in range(1, 5000)] + [(i, i + 1) for i in range(1, 4999, 2)])
+    else:
+        g, _ = gg.disjoint_union([gg.rmat(10, 16, seed=s) for s in range(4)] + [gg.from_edges(3, [(0, 1)])])
+    cn = oracle.common_counts(g)
+    dg = ctx.load(g)
+    try:
+        for strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH):
+            dg.set_strategy(strategy)
+            for (p, q, mu) in [(1, 5, 2), (1, 2, 3), (7, 10, 5)]:
+                assert_same(dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE), oracle.scan_from_counts(g, cn, p, q, mu),
+                            f"{which} strategy {strategy} eps={p}/{q} mu={mu}")
+            dg.query(1, 2, 2, ps.SCAN_Q_BUILD_CACHE)
+            got = dg.counts()
+            assert np.array_equal(got, cn), f"{which} strategy {strategy}: counts differ"
+            dg.drop_cache()
+        with pytest.raises(ps.ScanError):
+            dg.set_strategy(7)
+    finally:
+        dg.free()
+
+
 def test_query_entry_points_agree(ps, ctx):
     g = gg.rmat(12, 16, seed=9)
     dg = ctx.load(g)
