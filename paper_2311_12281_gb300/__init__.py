@@ -45,6 +45,18 @@ class scan_params(ctypes.Structure):
     _fields_ = [("eps_num", ctypes.c_uint32), ("eps_den", ctypes.c_uint32), ("mu", ctypes.c_uint32)]
 
 
+class scan_server_opts(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("use_cache", ctypes.c_int32)]
+
+
+class scan_server_report(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("throughput_rps", ctypes.c_double),
+                ("cache_builds", ctypes.c_uint64), ("cache_evictions", ctypes.c_uint64),
+                ("graph_loads", ctypes.c_uint64), ("graph_evictions", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+
+
 class scan_device_out(ctypes.Structure):
     _fields_ = [("core", ctypes.c_void_p), ("cid", ctypes.c_void_p), ("label", ctypes.c_void_p),
                 ("pairs", ctypes.c_void_p), ("pairs_cap", ctypes.c_int64), ("npairs", ctypes.c_void_p)]
@@ -84,6 +96,15 @@ SIGNATURES = {
     "scan_batch_free": (None, [_VP]),
     "scan_query_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "scan_common_counts_static": (ctypes.c_int, [_VP, _VP, _I32, _I64, _VP, _VP]),
+    "scan_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(scan_server_opts), _PP]),
+    "scan_server_add_graph": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
+    "scan_server_submit": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(scan_params), ctypes.POINTER(ctypes.c_uint64)]),
+    "scan_server_wait": (ctypes.c_int, [_VP, _U64, _PP, ctypes.POINTER(ctypes.c_double)]),
+    "scan_server_poll": (ctypes.c_int, [_VP, _U64, _PP, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "scan_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(scan_server_report)]),
+    "scan_server_reset_stats": (ctypes.c_int, [_VP]),
+    "scan_server_destroy": (None, [_VP]),
     "scan_result_n": (_I32, [_VP]),
     "scan_result_core": (_VP, [_VP]),
     "scan_result_cluster": (_VP, [_VP]),
@@ -322,6 +343,62 @@ def scan_common_counts_static(offsets: int, adj: int, n: int, nnz: int, cn: int,
     allocating nothing (all arguments are device addresses). For callers that
     cannot allocate device memory; see include/scan.h for the size limit."""
     _check(lib().scan_common_counts_static(offsets, adj, int(n), int(nnz), cn, stream))
+
+
+def scan_server_create(ctx: int, max_inflight: int = 8, use_cache: bool = True) -> int:
+    out = ctypes.c_void_p()
+    opts = scan_server_opts(int(max_inflight), 1 if use_cache else 0)
+    _check(lib().scan_server_create(ctx, ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def scan_server_add_graph(srv: int, graph) -> int:
+    off = np.ascontiguousarray(graph.offsets, dtype=np.int64)
+    adj = np.ascontiguousarray(graph.adj, dtype=np.int32)
+    gid = ctypes.c_int32()
+    _check(lib().scan_server_add_graph(srv, int(graph.n), off.ctypes.data, adj.ctypes.data if adj.size else None,
+                                       int(adj.size), ctypes.byref(gid)))
+    return gid.value
+
+
+def scan_server_submit(srv: int, graph_id: int, eps_num: int, eps_den: int, mu: int) -> int:
+    t = ctypes.c_uint64()
+    p = scan_params(int(eps_num), int(eps_den), int(mu))
+    _check(lib().scan_server_submit(srv, int(graph_id), ctypes.byref(p), ctypes.byref(t)))
+    return t.value
+
+
+def scan_server_wait(srv: int, ticket: int) -> tuple[dict, float]:
+    out = ctypes.c_void_p()
+    lat = ctypes.c_double()
+    _check(lib().scan_server_wait(srv, ctypes.c_uint64(ticket), ctypes.byref(out), ctypes.byref(lat)))
+    return _result_to_numpy(out.value), lat.value
+
+
+def scan_server_poll(srv: int, ticket: int):
+    """None while running, else (result, latency_ms)."""
+    out = ctypes.c_void_p()
+    lat = ctypes.c_double()
+    ready = ctypes.c_int32()
+    _check(lib().scan_server_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(out), ctypes.byref(lat),
+                                  ctypes.byref(ready)))
+    if not ready.value:
+        return None
+    return _result_to_numpy(out.value), lat.value
+
+
+def scan_server_stats(srv: int) -> dict:
+    r = scan_server_report()
+    _check(lib().scan_server_stats(srv, ctypes.byref(r)))
+    return {name: getattr(r, name) for name, _ in scan_server_report._fields_}
+
+
+def scan_server_reset_stats(srv: int):
+    _check(lib().scan_server_reset_stats(srv))
+
+
+def scan_server_destroy(srv: int):
+    lib().scan_server_destroy(srv)
 
 
 # --------------------------------------------------------------- convenience

@@ -49,6 +49,21 @@ __device__ __forceinline__ void ftab_insert(unsigned long long *t, int logc, int
     }
 }
 
+// Membership filter in front of the table: one bit per hashed id (a
+// different hash from the table's), about 32 bits per element, so most
+// probes of absent ids end after one shared-memory load.
+__device__ __forceinline__ uint32_t fbit(int32_t x, int logb) { return ((uint32_t)x * 0x85EBCA6Bu) >> (32 - logb); }
+
+__device__ __forceinline__ void fbits_set(uint32_t *bm, int logb, int32_t x) {
+    const uint32_t h = fbit(x, logb);
+    atomicOr(bm + (h >> 5), 1u << (h & 31));
+}
+
+__device__ __forceinline__ bool fbits_has(const uint32_t *bm, int logb, int32_t x) {
+    const uint32_t h = fbit(x, logb);
+    return (bm[h >> 5] >> (h & 31)) & 1u;
+}
+
 // index of key in the table, or -1
 __device__ __forceinline__ int32_t ftab_find(const unsigned long long *t, int logc, int32_t key) {
     const uint32_t mask = (1u << logc) - 1u;
@@ -63,6 +78,22 @@ __device__ __forceinline__ int32_t ftab_find(const unsigned long long *t, int lo
 }
 
 __device__ __forceinline__ int fceil_log2(int x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
+
+__device__ __forceinline__ unsigned long long rank_key(const int32_t *__restrict__ deg, int32_t x) {
+    return ((unsigned long long)(uint32_t)deg[x] << 32) | (uint32_t)x;
+}
+
+// first index of a rank-sorted row whose (deg, id) key is >= key
+__device__ __forceinline__ int32_t rank_lower_bound(const int32_t *__restrict__ r, int32_t len,
+                                                    const int32_t *__restrict__ deg, unsigned long long key) {
+    int32_t lo = 0, hi = len;
+    for (int it = 0; it < 40 && lo < hi; ++it) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (rank_key(deg, __ldg(r + mid)) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ int32_t lower_bound_row(const int32_t *__restrict__ r, int32_t len, int32_t x) {
     int32_t lo = 0, hi = len;
@@ -79,7 +110,7 @@ __device__ __forceinline__ int32_t lower_bound_row(const int32_t *__restrict__ r
 template <int UNROLL>
 __device__ __forceinline__ int probe_run(const int32_t *__restrict__ row, int32_t *__restrict__ cnt_row, int32_t k0,
                                          int32_t k1, int32_t step, const unsigned long long *t, int logc,
-                                         int32_t *ocnt) {
+                                         const uint32_t *bm, int logb, int32_t *ocnt) {
     int c = 0;
     for (int32_t kb = k0; kb < k1; kb += step * UNROLL) {
         int32_t x[UNROLL];
@@ -91,7 +122,7 @@ __device__ __forceinline__ int probe_run(const int32_t *__restrict__ row, int32_
 #pragma unroll
         for (int j = 0; j < UNROLL; ++j) {
             const int32_t k = kb + j * step;
-            if (k < k1) {
+            if (k < k1 && fbits_has(bm, logb, x[j])) {
                 const int32_t idx = ftab_find(t, logc, x[j]);
                 if (idx >= 0) {
                     ++c;
@@ -109,11 +140,13 @@ __global__ void __launch_bounds__(256) k_fwd_small(const int32_t *__restrict__ o
                                                    const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                                    const int32_t *__restrict__ deg, const int64_t *__restrict__ foff,
                                                    const int32_t *__restrict__ fadj, const uint32_t *__restrict__ fin,
-                                                   int32_t *__restrict__ fcnt) {
+                                                   int32_t *__restrict__ fcnt, int rank_sorted) {
     __shared__ unsigned long long tables[8][kFwdSmallTable];
+    __shared__ uint32_t bitmaps[8][64];
     __shared__ int32_t ocnts[8][kFwdSmallOut];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long *t = tables[wid];
+    uint32_t *bm = bitmaps[wid];
     int32_t *ocnt = ocnts[wid];
     const int warps_total = gridDim.x * 8;
     for (int32_t i = blockIdx.x * 8 + wid; i < nown; i += warps_total) {
@@ -121,33 +154,45 @@ __global__ void __launch_bounds__(256) k_fwd_small(const int32_t *__restrict__ o
         const int64_t fb = foff[b];
         const int32_t db = deg[b], ob = (int32_t)(foff[b + 1] - fb);
         const int logc = max(5, fceil_log2(4 * ob));
+        const int logb = max(5, fceil_log2(32 * ob));  // <= 2048 bits
         for (int k = lane; k < (1 << logc); k += kWarp) t[k] = kSlotEmpty;
+        for (int k = lane; k < (1 << (logb - 5)); k += kWarp) bm[k] = 0u;
         for (int k = lane; k < kFwdSmallOut; k += kWarp) ocnt[k] = 0;
         __syncwarp();
-        for (int k = lane; k < ob; k += kWarp) ftab_insert(t, logc, fadj[fb + k], k);
+        for (int k = lane; k < ob; k += kWarp) {
+            const int32_t x = fadj[fb + k];
+            ftab_insert(t, logc, x, k);
+            fbits_set(bm, logb, x);
+        }
         __syncwarp();
         const int64_t rb = off[b];
         for (int32_t g0 = 0; g0 < db; g0 += kWarp) {
             const int64_t s = rb + g0 + lane;
-            int32_t a = -1, oa = 0;
+            int32_t oa = 0, st = 0;
             int64_t fa = 0;
             if (g0 + lane < db) {
-                a = adj[s];
+                const int32_t a = adj[s];
                 const int32_t da = deg[a];
                 if (dev::rank_less(da, a, db, b)) {
                     fa = foff[a];
                     oa = (int32_t)(foff[a + 1] - fa);
+                    // a rank-sorted out(a) holds b's common neighbours above b only
+                    if (rank_sorted) st = (int32_t)((int64_t)fin[s] - fa) + 1;
                 }
             }
+            const int32_t len = oa - st;
             int mine = 0;
-            if (oa > 0 && oa < 16) mine = probe_run<4>(fadj + fa, fcnt + fa, 0, oa, 1, t, logc, ocnt);
-            unsigned longs = __ballot_sync(0xffffffffu, oa >= 16);
+            if (len > 0 && len < 16)
+                mine = probe_run<4>(fadj + fa, fcnt + fa, st, oa, 1, t, logc, bm, logb, ocnt);
+            unsigned longs = __ballot_sync(0xffffffffu, len >= 16);
             while (longs) {
                 const int src = __ffs(longs) - 1;
                 longs &= longs - 1;
                 const int64_t fas = __shfl_sync(0xffffffffu, fa, src);
                 const int32_t oas = __shfl_sync(0xffffffffu, oa, src);
-                int c = probe_run<kFwdUnroll>(fadj + fas, fcnt + fas, lane, oas, kWarp, t, logc, ocnt);
+                const int32_t sts = __shfl_sync(0xffffffffu, st, src);
+                int c = probe_run<kFwdUnroll>(fadj + fas, fcnt + fas, sts + lane, oas, kWarp, t, logc, bm, logb,
+                                              ocnt);
                 c = __reduce_add_sync(0xffffffffu, c);
                 if (lane == src) mine = c;
             }
@@ -198,9 +243,10 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
                                                    const int32_t *__restrict__ adj, const int32_t *__restrict__ deg,
                                                    const int64_t *__restrict__ foff, const int32_t *__restrict__ fadj,
                                                    const uint32_t *__restrict__ fin, int32_t *__restrict__ fcnt,
-                                                   int cap_log) {
+                                                   int cap_log, int cap_logb, int rank_sorted) {
     extern __shared__ unsigned long long t[];
-    int32_t *ocnt = (int32_t *)(t + (1 << cap_log));
+    uint32_t *bm = (uint32_t *)(t + (1 << cap_log));
+    int32_t *ocnt = (int32_t *)(bm + (1 << (cap_logb - 5)));
     __shared__ int32_t w_s[BLOCK], w_start[BLOCK], w_len[BLOCK], w_cnt[BLOCK];
     __shared__ int64_t w_fa[BLOCK];
     __shared__ int32_t l_idx[BLOCK], l_poff[BLOCK + 1], s_idx[BLOCK];
@@ -214,13 +260,22 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
     const int32_t db = (int32_t)(off[b + 1] - rb), ob = (int32_t)(foff[b + 1] - fb);
     const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
     const bool chunked = ob > kFwdChunk;
+    // the chunk's bounds, as ids (id-sorted lists) or as rank keys (rank-sorted)
     const int32_t lo = tb == 0 ? INT32_MIN : fadj[fb + tb];
     const int32_t hi = te == ob ? INT32_MAX : fadj[fb + te];
+    const unsigned long long lo_key = tb == 0 ? 0ull : rank_key(deg, lo);
+    const unsigned long long hi_key = te == ob ? ~0ull : rank_key(deg, hi);
     const int logc = min(cap_log, max(5, fceil_log2(4 * tlen)));
+    const int logb = min(cap_logb, max(5, fceil_log2(32 * tlen)));
     for (int k = threadIdx.x; k < (1 << logc); k += BLOCK) t[k] = kSlotEmpty;
+    for (int k = threadIdx.x; k < (1 << (logb - 5)); k += BLOCK) bm[k] = 0u;
     for (int k = threadIdx.x; k < tlen; k += BLOCK) ocnt[k] = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) ftab_insert(t, logc, fadj[fb + tb + k], k);
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+        const int32_t x = fadj[fb + tb + k];
+        ftab_insert(t, logc, x, k);
+        fbits_set(bm, logb, x);
+    }
     const int lane = threadIdx.x & 31;
 
     for (int32_t r0 = it.sb; r0 < it.se; r0 += BLOCK) {
@@ -233,13 +288,21 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
             const int32_t a = adj[s], da = deg[a];
             if (dev::rank_less(da, a, db, b)) {
                 fa = foff[a];
-                len = (int32_t)(foff[a + 1] - fa);
-                if (chunked && len > 0) {
-                    const int32_t *row = fadj + fa;
-                    start = lo == INT32_MIN ? 0 : lower_bound_row(row, len, lo);
-                    const int32_t end = hi == INT32_MAX ? len : lower_bound_row(row, len, hi);
-                    len = end - start;
+                const int32_t oa = (int32_t)(foff[a + 1] - fa);
+                const int32_t *row = fadj + fa;
+                int32_t end = oa;
+                if (rank_sorted) {
+                    // common neighbours of a and b rank above b: the suffix after b
+                    start = (int32_t)((int64_t)fin[s] - fa) + 1;
+                    if (chunked) {
+                        start = max(start, rank_lower_bound(row, oa, deg, lo_key));
+                        end = hi_key == ~0ull ? oa : rank_lower_bound(row, oa, deg, hi_key);
+                    }
+                } else if (chunked && oa > 0) {
+                    start = lo == INT32_MIN ? 0 : lower_bound_row(row, oa, lo);
+                    end = hi == INT32_MAX ? oa : lower_bound_row(row, oa, hi);
                 }
+                len = end - start;
                 work = len > 0;
                 s32 = rel;
             }
@@ -290,7 +353,7 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
             const int32_t o = w_start[e] + (p - l_poff[li]) * kFwdPiece;
             const int32_t pend = min(o + kFwdPiece, w_start[e] + w_len[e]);
             const int64_t fa = w_fa[e];
-            int c = probe_run<kFwdUnroll>(fadj + fa, fcnt + fa, o + lane, pend, kWarp, t, logc, ocnt);
+            int c = probe_run<kFwdUnroll>(fadj + fa, fcnt + fa, o + lane, pend, kWarp, t, logc, bm, logb, ocnt);
             c = __reduce_add_sync(0xffffffffu, c);
             if (lane == 0 && c) atomicAdd(&w_cnt[e], c);
         }
@@ -303,7 +366,8 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
             if (k < n_short) {
                 const int32_t e = s_idx[k];
                 const int64_t fa = w_fa[e];
-                w_cnt[e] = probe_run<4>(fadj + fa, fcnt + fa, w_start[e], w_start[e] + w_len[e], 1, t, logc, ocnt);
+                w_cnt[e] = probe_run<4>(fadj + fa, fcnt + fa, w_start[e], w_start[e] + w_len[e], 1, t, logc, bm,
+                                        logb, ocnt);
             }
         }
         __syncthreads();
@@ -341,6 +405,95 @@ __global__ void k_fwd_finish(const uint32_t *__restrict__ oe, int64_t m, const i
 }
 
 // ------------------------------------------------------------ load time
+// Rank order inside every out-list: key (deg, id), carried with the slot id.
+constexpr int kSortMax = 4096;  // longest out-list sorted by rank (longer: all lists stay in id order)
+
+// warp per vertex with out-degree <= 32: bitonic sort in registers
+__global__ void k_fwd_sort_warp(const int64_t *__restrict__ foff, int32_t n, const int32_t *__restrict__ deg,
+                                int32_t *__restrict__ fadj, uint32_t *__restrict__ oe) {
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+    const int lane = threadIdx.x & 31;
+    if (a >= n) return;
+    const int64_t b = foff[a];
+    const int32_t len = (int32_t)(foff[a + 1] - b);
+    if (len < 2 || len > kWarp) return;
+    unsigned long long key = ~0ull;
+    uint32_t pay = 0;
+    if (lane < len) {
+        key = rank_key(deg, fadj[b + lane]);
+        pay = oe[b + lane];
+    }
+    for (int k = 2; k <= kWarp; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, j);
+            const uint32_t op = __shfl_xor_sync(0xffffffffu, pay, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            const bool take = lower == up ? ok < key : ok > key;
+            if (take) { key = ok; pay = op; }
+        }
+    if (lane < len) {
+        fadj[b + lane] = (int32_t)(uint32_t)key;
+        oe[b + lane] = pay;
+    }
+}
+
+// CTA per vertex with 32 < out-degree <= kSortMax: bitonic sort in shared memory
+__global__ void __launch_bounds__(1024) k_fwd_sort_cta(const int32_t *__restrict__ verts,
+                                                       const int64_t *__restrict__ foff,
+                                                       const int32_t *__restrict__ deg, int32_t *__restrict__ fadj,
+                                                       uint32_t *__restrict__ oe) {
+    __shared__ unsigned long long key[kSortMax];
+    __shared__ uint32_t pay[kSortMax];
+    const int32_t a = verts[blockIdx.x];
+    const int64_t b = foff[a];
+    const int32_t len = (int32_t)(foff[a + 1] - b);
+    int size = 64;
+    while (size < len) size <<= 1;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        key[i] = i < len ? rank_key(deg, fadj[b + i]) : ~0ull;
+        pay[i] = i < len ? oe[b + i] : 0u;
+    }
+    __syncthreads();
+    for (int k = 2; k <= size; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < size; i += blockDim.x) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    if ((key[i] > key[p]) == up) {
+                        const unsigned long long tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const uint32_t tp = pay[i];
+                        pay[i] = pay[p];
+                        pay[p] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        fadj[b + i] = (int32_t)(uint32_t)key[i];
+        oe[b + i] = pay[i];
+    }
+}
+
+__global__ void k_fwd_fin(const uint32_t *__restrict__ oe, int64_t m, const uint32_t *__restrict__ rev,
+                          uint32_t *__restrict__ fin) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        fin[rev[oe[i]]] = (uint32_t)i;
+}
+
+// vertices whose out-list needs the CTA sort; flags a list too long to sort
+__global__ void k_fwd_sort_pick(const int64_t *__restrict__ foff, int32_t n, int32_t *__restrict__ verts,
+                                unsigned long long *counts) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const int64_t len = foff[a + 1] - foff[a];
+    if (len > kSortMax) atomicAdd(counts + 1, 1ull);
+    else if (len > kWarp) verts[atomicAdd(counts + 0, 1ull)] = (int32_t)a;
+}
+
 __global__ void k_fwd_adj(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ adj,
                           const uint32_t *__restrict__ rev, int32_t *__restrict__ fadj, uint32_t *__restrict__ fin) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -424,10 +577,33 @@ scan_status fwd_prepare(Graph *g) {
         (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->adj.ptr, (const uint32_t *)g->rev.ptr,
         (int32_t *)g->fadj.ptr, (uint32_t *)g->fin.ptr);
     c->launches++;
-    // schedule
     DevBuf cnts;
     SCAN_TRY(dev_alloc(c, cnts, 4 * sizeof(unsigned long long)));
     auto *counts = (unsigned long long *)cnts.ptr;
+    // order every out-list by rank, carrying the slot ids, then re-index fin
+    {
+        SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
+        int32_t *verts = (int32_t *)g->cnt.ptr;  // scratch int32[n+1]
+        k_fwd_sort_pick<<<grid_for(n, 256), 256, 0, c->stream>>>((const int64_t *)g->foff.ptr, n, verts, counts);
+        unsigned long long h2[2];
+        SCAN_CUDA(cudaMemcpyAsync(h2, counts, sizeof(h2), cudaMemcpyDeviceToHost, c->stream));
+        SCAN_CUDA(cudaStreamSynchronize(c->stream));
+        c->launches++;
+        g->fwd_rank_sorted = h2[1] == 0;
+        if (g->fwd_rank_sorted) {
+            k_fwd_sort_warp<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(
+                (const int64_t *)g->foff.ptr, n, (const int32_t *)g->deg.ptr, (int32_t *)g->fadj.ptr,
+                (uint32_t *)g->oe.ptr);
+            if (h2[0] > 0)
+                k_fwd_sort_cta<<<(unsigned)h2[0], 1024, 0, c->stream>>>(verts, (const int64_t *)g->foff.ptr,
+                                                                       (const int32_t *)g->deg.ptr,
+                                                                       (int32_t *)g->fadj.ptr, (uint32_t *)g->oe.ptr);
+            k_fwd_fin<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
+                (const uint32_t *)g->oe.ptr, m, (const uint32_t *)g->rev.ptr, (uint32_t *)g->fin.ptr);
+            c->launches += 2 + (h2[0] > 0);
+        }
+    }
+    // schedule
     SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
     int32_t *nranges = (int32_t *)g->ucnt.ptr;  // scratch int32[n+1]
     k_fwd_sched_count<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(
@@ -473,27 +649,28 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     auto *fin = (const uint32_t *)g->fin.ptr;
     auto *fcnt = (int32_t *)g->fcnt.ptr;
     SCAN_CUDA(cudaMemsetAsync(fcnt, 0, 4 * (size_t)g->m, st));
-    if (g->fwd_items_n[2] > 0) {  // out-degree > 1024: 16384-slot tables
-        const int cap_log = 14;
-        const size_t smem = (8u << cap_log) + 4 * kFwdChunk;
+    const int rs = g->fwd_rank_sorted ? 1 : 0;
+    if (g->fwd_items_n[2] > 0) {  // out-degree > 1024: 16384-slot tables, 2^17-bit filters
+        const int cap_log = 14, cap_logb = 17;
+        const size_t smem = (8u << cap_log) + (1u << (cap_logb - 3)) + 4 * kFwdChunk;
         auto kern = k_fwd_cta<512>;
         SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<(unsigned)g->fwd_items_n[2], 512, smem, st>>>((const FItem *)g->fwd_items[2].ptr, off, adj, deg, foff,
-                                                           fadj, fin, fcnt, cap_log);
+                                                           fadj, fin, fcnt, cap_log, cap_logb, rs);
         c->launches++;
     }
-    if (g->fwd_items_n[1] > 0) {  // out-degree <= 1024: 4096-slot tables
-        const int cap_log = 12;
-        const size_t smem = (8u << cap_log) + 4 * 1024;
+    if (g->fwd_items_n[1] > 0) {  // out-degree <= 1024: 4096-slot tables, 2^15-bit filters
+        const int cap_log = 12, cap_logb = 15;
+        const size_t smem = (8u << cap_log) + (1u << (cap_logb - 3)) + 4 * 1024;
         auto kern = k_fwd_cta<512>;
         SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<(unsigned)g->fwd_items_n[1], 512, smem, st>>>((const FItem *)g->fwd_items[1].ptr, off, adj, deg, foff,
-                                                           fadj, fin, fcnt, cap_log);
+                                                           fadj, fin, fcnt, cap_log, cap_logb, rs);
         c->launches++;
     }
     if (g->fwd_small > 0) {
         k_fwd_small<<<grid_for((int64_t)g->fwd_small * kWarp, 256, c->num_sms * 16), 256, 0, st>>>(
-            (const int32_t *)g->fwd_owners.ptr, g->fwd_small, off, adj, deg, foff, fadj, fin, fcnt);
+            (const int32_t *)g->fwd_owners.ptr, g->fwd_small, off, adj, deg, foff, fadj, fin, fcnt, rs);
         c->launches++;
     }
     const unsigned gf = grid_for(g->m, 256, c->num_sms * 32);

@@ -66,6 +66,7 @@ struct Graph {
     int64_t fwd_items_n[3] = {0, 0, 0};
     int32_t fwd_small = 0;
     bool fwd_ready = false;
+    bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
     // per-query scratch
     DevBuf sim;             // uint8[nnz] 1 = eps-similar
