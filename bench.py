@@ -49,7 +49,17 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain GPU path comparator")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel choice (no autotuner)")
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
+    ap.add_argument("--workload", choices=["sweep", "batch", "serving"], default="sweep",
+                    help="sweep: the R-MAT scale-22 sweep (default, the headline line); batch: 4,096 "
+                         "Chung-Lu graphs in one pass; serving: Poisson query streams against the server")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--rates", default="200,1000,5000", help="serving arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving requests per rate")
+    ap.add_argument("--big-n", type=int, default=16_000_000, help="serving: vertices of the big Chung-Lu graph")
+    ap.add_argument("--big-deg", type=float, default=72.0, help="serving: mean sampled degree of the big graph")
+    ap.add_argument("--pool", type=int, default=256, help="serving: R-MAT pool graphs (scales 12-18)")
     return ap.parse_args()
 
 
@@ -86,7 +96,25 @@ def algorithmic_bytes(g, dmin1, dmax1, p, q):
 
 
 def full_count_bytes(g, dmin1):
+    """Per-edge full count: the smaller row of every edge, every row once as
+    the larger side, counts written to both slots, offsets."""
     return 4.0 * float((dmin1 - 1).sum()) + 4.0 * g.nnz + 4.0 * g.nnz + 8.0 * (g.n + 1)
+
+
+def forward_bytes(g):
+    """Degree-oriented triangle count for one query: every oriented edge a->b
+    streams the part of out(a) above b (sum over a of d+(d+-1)/2 ids), each
+    owner's out-list once, the owner-row planning reads (id, degree, forward
+    index: 12 B per slot), the per-edge counter cleared, updated once per
+    edge and read back (12 B per oriented edge), one similarity byte per slot
+    and the offsets. Triangle atomics are not counted."""
+    deg = g.degrees()
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dst = g.adj.astype(np.int64)
+    fwd = (deg[dst] > deg[src]) | ((deg[dst] == deg[src]) & (dst > src))
+    dplus = np.bincount(src[fwd], minlength=g.n).astype(np.float64)
+    suffix = float((dplus * (dplus - 1) / 2).sum())
+    return 4.0 * suffix + 4.0 * g.m + 12.0 * g.nnz + 12.0 * g.m + 1.0 * g.nnz + 8.0 * (g.n + 1)
 
 
 # --------------------------------------------------------------- clocks
@@ -186,11 +214,180 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- batch
+def run_batch(args):
+    """4,096 Chung-Lu graphs (exponent 2.1, n log-uniform in [100, 50000], mean
+    degree uniform in [4, 64]), each with its own eps = p/20 and mu, clustered
+    together in one pass over the resident union (kernel family and schedule
+    sizes from the autotuner), against a loop of per-graph queries."""
+    import torch
+
+    import paper_2311_12281_gb300 as ps
+    from paper_2311_12281_gb300 import _build
+
+    _build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    graphs, specs = gg.chung_lu_batch(args.batch_count)
+    params = [(s["eps"][0], s["eps"][1], s["mu"]) for s in specs]
+    total_m = sum(g.m for g in graphs)
+    ctx = ps.Context(0, stream=stream.cuda_stream)
+    b = ps.scan_batch_load(ctx.handle, graphs)
+    ug = ps.scan_batch_union(b)
+    strategy, tune_ms = ps.scan_graph_autotune(ug, os.path.join(ROOT, "_autotune_cache.txt"))
+    n = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
+    core = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cid = torch.empty(n, dtype=torch.int32, device="cuda")
+    label = torch.empty(n, dtype=torch.uint8, device="cuda")
+    pairs = torch.empty(2 * max(nnz, 1), dtype=torch.int32, device="cuda")
+    npairs = torch.empty(1, dtype=torch.int64, device="cuda")
+
+    def step():
+        ps.scan_batch_query_device(b, params, ps.SCAN_Q_RECOMPUTE, core.data_ptr(), cid.data_ptr(), label.data_ptr(),
+                                   pairs.data_ptr(), nnz, npairs.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = ctx.kernel_launches
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    launches = ctx.kernel_launches - launches0
+    clk = clocks.stop()
+
+    # comparator: one graph per launch sequence (each graph loaded alone)
+    loop_graphs = [ctx.load(gr) for gr in graphs]
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for gh, gr, (p, q, mu) in zip(loop_graphs, graphs, params):
+        ps.scan_query_device(gh.handle, p, q, mu, ps.SCAN_Q_PLAIN, core.data_ptr(), cid.data_ptr(), label.data_ptr(),
+                             pairs.data_ptr(), nnz, npairs.data_ptr())
+    z.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = a.elapsed_time(z)
+    for gh in loop_graphs:
+        gh.free()
+
+    # end to end: host CSRs in, host results out, every step
+    t = time.perf_counter()
+    bh = ps.scan_batch_load(ctx.handle, graphs)
+    res = ps.scan_batch_query(bh, params)
+    ps.scan_batch_free(bh)
+    e2e_s = time.perf_counter() - t
+    h2d = sum(gr.offsets.nbytes + gr.adj.nbytes for gr in graphs)
+    d2h = sum(r["core"].nbytes + r["cid"].nbytes + r["label"].nbytes + r["pairs"].nbytes for r in res)
+    ps.scan_batch_free(b)
+    ctx.close()
+    line = {"metric": METRIC, "value": total_m / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"chung_lu_batch{args.batch_count}", "graphs": len(graphs), "n": n,
+                       "m": total_m, "per_graph_params": True, "strategy": strategy, "autotune_ms": tune_ms,
+                       "l2": "inputs larger than L2, no flush"},
+            "per_graph_loop": {"value": total_m / (loop_ms / 1e3), "unit": UNIT, "ms_per_step": loop_ms,
+                               "what": "one graph per launch sequence, binary-search path"},
+            "gpu_launches": launches, "clocks": clk,
+            "e2e": {"value": total_m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "s_per_step": e2e_s}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- serving
+def run_serving(args):
+    """A resident Chung-Lu graph (16M vertices) plus a pool of R-MAT graphs
+    (scale k mod 7 + 12, edge factor 16, seed 4000+k) behind the query server;
+    open-loop Poisson arrivals (seed 44) at each rate, 1/8 of the requests to
+    the big graph and 7/8 uniform over the pool, eps = p/20 with p uniform in
+    4..16 and mu uniform in 2..10. Every graph is queried once before timing
+    (cold: load and count cache); then each rate runs against the cached
+    server and against the plain path (no cache, one request at a time)."""
+    import paper_2311_12281_gb300 as ps
+    from paper_2311_12281_gb300 import _build
+
+    _build.build()
+    t = time.perf_counter()
+    big = gg.chung_lu(args.big_n, args.big_deg, 2.1, seed=4)
+    pool = [gg.rmat(k % 7 + 12, 16, seed=4000 + k) for k in range(args.pool)]
+    gen_s = time.perf_counter() - t
+    graphs = [big] + pool
+    rng = np.random.default_rng(44)
+
+    def make_requests(count):
+        target = np.where(rng.random(count) < 1 / 8, 0, 1 + rng.integers(0, len(pool), count))
+        p = rng.integers(4, 17, count)
+        mu = rng.integers(2, 11, count)
+        return [(int(a), int(b), 20, int(c)) for a, b, c in zip(target, p, mu)]
+
+    def run(srv, ids, reqs, rate, max_wall_s):
+        gaps = rng.exponential(1.0 / rate, len(reqs))
+        ps.scan_server_reset_stats(srv)
+        tickets = []
+        t_start = time.perf_counter()
+        due = t_start
+        for gap, (gi, p, q, mu) in zip(gaps, reqs):
+            due += gap
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-4:
+                    time.sleep(min(due - now - 1e-4, 0.01))
+            tickets.append(ps.scan_server_submit(srv, ids[gi], p, q, mu))
+            if time.perf_counter() - t_start > max_wall_s:
+                break
+        for tk in tickets:
+            ps.scan_server_wait(srv, tk)
+        st = ps.scan_server_stats(srv)
+        st["submitted"] = len(tickets)
+        return st
+
+    out = {}
+    for label, cache, slots in (("cached", True, 16), ("plain", False, 1)):
+        ctx = ps.scan_ctx_create(0)
+        srv = ps.scan_server_create(ctx, max_inflight=slots, use_cache=cache)
+        ids = [ps.scan_server_add_graph(srv, gr) for gr in graphs]
+        # cold pass: one query per graph (load, and the count cache when on)
+        tc = time.perf_counter()
+        for gid in ids:
+            ps.scan_server_wait(srv, ps.scan_server_submit(srv, gid, 1, 2, 3))
+        cold = ps.scan_server_stats(srv)
+        cold["wall_s"] = time.perf_counter() - tc
+        per_rate = {}
+        for rate in [int(x) for x in args.rates.split(",")]:
+            reqs = make_requests(args.requests if cache else max(50, args.requests // 10))
+            per_rate[str(rate)] = run(srv, ids, reqs, rate, 60.0)
+        ps.scan_server_destroy(srv)
+        ps.scan_ctx_destroy(ctx)
+        out[label] = {"cold": cold, "rates": per_rate}
+    line = {"metric": "serving p50 query latency", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "value": out["cached"]["rates"][args.rates.split(",")[0]]["p50_ms"], "data": "synthetic",
+            "dtype": "i32", "vs_baseline": None,
+            "config": {"workload": "serving", "big": {"n": big.n, "m": big.m}, "pool": len(pool),
+                       "requests_per_rate": args.requests, "generation_s": gen_s},
+            "cached": out["cached"], "plain": out["plain"],
+            "p50_speedup": {r: (out["plain"]["rates"][r]["p50_ms"] / out["cached"]["rates"][r]["p50_ms"])
+                            if out["cached"]["rates"][r]["p50_ms"] else None for r in out["cached"]["rates"]}}
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- ours
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
 
@@ -219,6 +416,10 @@ def main():
 
     ctx = ps.Context(local, stream=stream.cuda_stream)
     dg = ctx.load(g)
+    tuned = None
+    if args.mode == "recompute" and not args.no_tune:
+        # kernel family and schedule sizes from the autotuner (outside the timed region)
+        tuned = ps.scan_graph_autotune(dg.handle, os.path.join(ROOT, "_autotune_cache.txt"))
     if args.mode == "cache":
         dg.query(1, 2, 2, ps.SCAN_Q_BUILD_CACHE)
     n = g.n
@@ -266,11 +467,20 @@ def main():
 
     # roofline of the similarity stage (the dominant kernel)
     sim_ms, sim_n = stage_ms["similarity"]
-    if args.mode == "recompute":
-        b_step = sum(algorithmic_bytes(g, dmin1, dmax1, p, q) for (p, q, mu) in queries)
+    strategy = ps.scan_graph_strategy(dg.handle)
+    per_edge_pruned = sum(algorithmic_bytes(g, dmin1, dmax1, p, q) for (p, q, mu) in queries)
+    if args.mode == "recompute" and strategy == ps.SCAN_STRATEGY_FORWARD:
+        b_step = forward_bytes(g) * len(queries)
+        bytes_def = "forward triangle count: streamed out-list suffixes + owner lists + planning + counters"
+    elif args.mode == "recompute":
+        b_step = per_edge_pruned
+        bytes_def = "per-edge intersection of the edges the degrees do not decide"
     else:
         b_step = full_count_bytes(g, dmin1) * (len(queries) if args.mode == "plain" else 0)
+        bytes_def = "per-edge full count"
     achieved = (b_step * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    # the per-edge intersection's bytes for the same queries, as a problem-level reference
+    problem_rate = (per_edge_pruned * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -295,11 +505,14 @@ def main():
         "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), seed 2",
                    "n": g.n, "m": g.m, "queries_per_step": len(queries), "mode": args.mode,
                    "parallelism": "replicas" if world > 1 else "single",
+                   "autotuned": {"strategy": tuned[0], "count_ms": tuned[1]} if tuned else None,
                    "l2": "inputs larger than L2 (adjacency 513 MB), no flush"},
         "roofline": {"bound": "hbm", "kernel": "similarity stage", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "bytes_per_step": b_step, "launches": sim_n,
-                     "avg_ms": sim_ms / max(sim_n, 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                     "bytes_per_step": b_step, "bytes_def": bytes_def, "launches": sim_n,
+                     "avg_ms": sim_ms / max(sim_n, 1), "strategy": strategy,
+                     "per_edge_bytes_rate_gbs": problem_rate,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage_ms.items()},
         "gpu_launches": launches,
         "clocks": clk,

@@ -125,6 +125,24 @@ SCAN_API scan_status scan_ctx_stage_time(scan_ctx *ctx, int32_t stage, double *t
 SCAN_API scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj,
                             int64_t nnz, uint32_t flags, scan_graph **out);
 SCAN_API void scan_graph_free(scan_graph *g);
+/*
+ * Out of core (the paper's Section 5 setting: vertices fit on the device,
+ * edges do not): the CSR stays in the caller's host memory -- pinned by the
+ * library if it is not already, and kept alive and unmodified by the caller
+ * until scan_graph_free -- and every query streams it in contiguous row
+ * blocks of at most block_slots slots (0: sized from the context's budget
+ * left after the per-vertex state). Lemma 5.1 makes the result equal the
+ * resident one: an edge's similarity needs only its two endpoints' rows.
+ * Validation as scan_graph_load (symmetry found missing during a query is
+ * reported then). Queries: scan_query / scan_query_ex (every mode is a full
+ * recompute); the cache, strategy and device-output calls return SCAN_EINVAL.
+ * scan_graph_load with SCAN_LOAD_PINNED_BORROW is this call with block_slots 0.
+ */
+SCAN_API scan_status scan_graph_load_partitioned(scan_ctx *ctx, int32_t n, const int64_t *offsets,
+                                                 const int32_t *adj, int64_t nnz, int64_t block_slots,
+                                                 scan_graph **out);
+/* Number of row blocks of a partitioned graph (0 for a resident one). */
+SCAN_API int32_t scan_graph_blocks(const scan_graph *g);
 SCAN_API int32_t scan_graph_n(const scan_graph *g);
 SCAN_API int64_t scan_graph_nnz(const scan_graph *g);
 /* Device bytes held by this graph (including its count cache). */
@@ -159,6 +177,15 @@ typedef struct scan_params {
  * pruning). SCAN_EINVAL for an unknown value. */
 SCAN_API scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy);
 SCAN_API int32_t scan_graph_strategy(const scan_graph *g);
+/* Autotuner: times one full count of this graph with every kernel family
+ * and a few work-item sizes of the forward schedule, keeps the fastest, and
+ * appends the choice to the text file cache_path (NULL: not stored) under a
+ * key of the graph's shape (log2 of n, nnz and the maximum degree). A later
+ * call on a graph with the same key takes the stored choice without timing.
+ * *strategy_out / *ms_out (may be NULL) receive the choice and its time.
+ * Leaves no count cache behind unless the graph had one. Synchronous. */
+SCAN_API scan_status scan_graph_autotune(scan_graph *g, const char *cache_path, int32_t *strategy_out,
+                                         double *ms_out);
 
 /* Query modes. */
 #define SCAN_Q_AUTO 0x0u        /* use the count cache if present, else full recompute */

@@ -77,6 +77,8 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_int64)]),
     "scan_graph_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _U32, _PP]),
     "scan_graph_free": (None, [_VP]),
+    "scan_graph_load_partitioned": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _I64, _PP]),
+    "scan_graph_blocks": (_I32, [_VP]),
     "scan_graph_n": (_I32, [_VP]),
     "scan_graph_nnz": (_I64, [_VP]),
     "scan_graph_device_bytes": (_U64, [_VP]),
@@ -85,6 +87,8 @@ SIGNATURES = {
     "scan_graph_copy_counts": (ctypes.c_int, [_VP, _VP]),
     "scan_graph_set_strategy": (ctypes.c_int, [_VP, _I32]),
     "scan_graph_strategy": (_I32, [_VP]),
+    "scan_graph_autotune": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "scan_query": (ctypes.c_int, [_VP, _U32, _U32, _U32, _PP]),
     "scan_query_ex": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, _PP]),
     "scan_query_device": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, ctypes.POINTER(scan_device_out)]),
@@ -202,6 +206,22 @@ def scan_graph_free(g: int):
     lib().scan_graph_free(g)
 
 
+def scan_graph_load_partitioned(ctx: int, n: int, offsets: np.ndarray, adj: np.ndarray,
+                                block_slots: int = 0) -> int:
+    """Out-of-core graph: offsets/adj are host arrays that must stay alive and
+    unchanged until scan_graph_free (the caller keeps a reference)."""
+    assert offsets.dtype == np.int64 and adj.dtype == np.int32
+    assert offsets.flags["C_CONTIGUOUS"] and adj.flags["C_CONTIGUOUS"]
+    out = ctypes.c_void_p()
+    _check(lib().scan_graph_load_partitioned(ctx, int(n), offsets.ctypes.data, adj.ctypes.data if adj.size else None,
+                                             int(adj.size), int(block_slots), ctypes.byref(out)))
+    return out.value
+
+
+def scan_graph_blocks(g: int) -> int:
+    return int(lib().scan_graph_blocks(g))
+
+
 def scan_graph_n(g: int) -> int:
     return int(lib().scan_graph_n(g))
 
@@ -231,6 +251,15 @@ def scan_graph_set_strategy(g: int, strategy: int):
 
 def scan_graph_strategy(g: int) -> int:
     return int(lib().scan_graph_strategy(g))
+
+
+def scan_graph_autotune(g: int, cache_path: str | None = None) -> tuple[int, float]:
+    """Time the kernel families on this graph, keep the fastest; returns (strategy, ms)."""
+    st = ctypes.c_int32()
+    ms = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().scan_graph_autotune(g, path, ctypes.byref(st), ctypes.byref(ms)))
+    return st.value, ms.value
 
 
 def scan_graph_copy_counts(g: int, nnz: int) -> np.ndarray:
@@ -410,7 +439,21 @@ class Context:
         self._graphs = []
 
     def load(self, graph, flags: int = 0) -> "Graph":
-        g = Graph(self, scan_graph_load(self.handle, graph.n, graph.offsets, graph.adj, None, flags), graph.n)
+        off = np.ascontiguousarray(graph.offsets, dtype=np.int64)
+        adj = np.ascontiguousarray(graph.adj, dtype=np.int32)
+        g = Graph(self, scan_graph_load(self.handle, graph.n, off, adj, None, flags), graph.n)
+        if flags & SCAN_LOAD_PINNED_BORROW:
+            g._host = (off, adj)  # borrowed by the library until free
+        self._graphs.append(g)
+        return g
+
+    def load_partitioned(self, graph, block_slots: int = 0) -> "Graph":
+        """Out-of-core load: the graph's host arrays stay referenced by the
+        returned object until it is freed (the library streams from them)."""
+        off = np.ascontiguousarray(graph.offsets, dtype=np.int64)
+        adj = np.ascontiguousarray(graph.adj, dtype=np.int32)
+        g = Graph(self, scan_graph_load_partitioned(self.handle, graph.n, off, adj, block_slots), graph.n)
+        g._host = (off, adj)
         self._graphs.append(g)
         return g
 
@@ -443,6 +486,7 @@ class Context:
 class Graph:
     def __init__(self, ctx: Context, handle: int, n: int):
         self.ctx, self.handle, self.n = ctx, handle, n
+        self._host = None
 
     def query(self, eps_num: int, eps_den: int, mu: int, mode: int = SCAN_Q_AUTO) -> dict:
         return scan_query_ex(self.handle, eps_num, eps_den, mu, mode)
@@ -460,7 +504,12 @@ class Graph:
     def has_cache(self) -> bool:
         return scan_graph_has_cache(self.handle)
 
+    @property
+    def blocks(self) -> int:
+        return scan_graph_blocks(self.handle)
+
     def free(self):
         if self.handle:
             scan_graph_free(self.handle)
             self.handle = None
+        self._host = None

@@ -261,6 +261,7 @@ void graph_destroy(Graph *g) {
     if (!g) return;
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
+    if (g->part) part_release(g);
     graph_release(g);
     delete static_cast<scan_graph *>(g);
 }
@@ -302,15 +303,33 @@ scan_status scan_graph_load(scan_ctx *ctx, int32_t n, const int64_t *offsets, co
     ABI_GUARD_BEGIN
     if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
     *out = nullptr;
-    if (flags & SCAN_LOAD_PINNED_BORROW) {
-        set_error("SCAN_LOAD_PINNED_BORROW is not available in this build");
-        return SCAN_EINVAL;
-    }
     Graph *g = nullptr;
-    SCAN_TRY(graph_create(ctx, n, offsets, adj, nnz, (flags & SCAN_LOAD_DEVICE_PTRS) != 0, &g));
+    if (flags & SCAN_LOAD_PINNED_BORROW) {
+        if (flags & SCAN_LOAD_DEVICE_PTRS) { set_error("a partitioned graph takes host arrays"); return SCAN_EINVAL; }
+        SCAN_TRY(part_create(ctx, n, offsets, adj, nnz, &g, 0));
+    } else {
+        SCAN_TRY(graph_create(ctx, n, offsets, adj, nnz, (flags & SCAN_LOAD_DEVICE_PTRS) != 0, &g));
+    }
     *out = static_cast<scan_graph *>(g);
     return SCAN_OK;
     ABI_GUARD_END
+}
+
+scan_status scan_graph_load_partitioned(scan_ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj,
+                                        int64_t nnz, int64_t block_slots, scan_graph **out) {
+    ABI_GUARD_BEGIN
+    if (!ctx || !out) { set_error("ctx or out is NULL"); return SCAN_EINVAL; }
+    *out = nullptr;
+    if (block_slots < 0) { set_error("block_slots must be >= 0"); return SCAN_EINVAL; }
+    Graph *g = nullptr;
+    SCAN_TRY(part_create(ctx, n, offsets, adj, nnz, &g, block_slots));
+    *out = static_cast<scan_graph *>(g);
+    return SCAN_OK;
+    ABI_GUARD_END
+}
+
+int32_t scan_graph_blocks(const scan_graph *g) {
+    return g && g->part ? part_block_count(g) : 0;
 }
 
 void scan_graph_free(scan_graph *g) { graph_destroy(g); }
@@ -338,6 +357,7 @@ int32_t scan_graph_has_cache(const scan_graph *g) { return g && g->cache_valid ?
 
 scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy) {
     if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
+    if (g->part) { set_error("not available for a partitioned graph"); return SCAN_EINVAL; }
     if (strategy != SCAN_STRATEGY_FORWARD && strategy != SCAN_STRATEGY_OWNER && strategy != SCAN_STRATEGY_BSEARCH) {
         set_error("unknown strategy " + std::to_string(strategy));
         return SCAN_EINVAL;
@@ -350,7 +370,7 @@ int32_t scan_graph_strategy(const scan_graph *g) { return g ? g->strategy : -1; 
 
 scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out) {
     if (!g || !out) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
-    if (!g->cache_valid) { set_error("graph has no common-count cache"); return SCAN_EINVAL; }
+    if (g->part || !g->cache_valid) { set_error("graph has no common-count cache"); return SCAN_EINVAL; }
     SCAN_CUDA(cudaSetDevice(g->ctx->device));
     if (g->nnz > 0)
         SCAN_CUDA(cudaMemcpyAsync(out, g->cn_cache.ptr, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost,
@@ -363,6 +383,7 @@ scan_status scan_query_device(scan_graph *g, const scan_params *params, uint32_t
     ABI_GUARD_BEGIN
     if (!g || !o) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
     SCAN_TRY(check_params(params));
+    if (g->part) { set_error("a partitioned graph answers through scan_query / scan_query_ex"); return SCAN_EINVAL; }
     if (g->n > 0 && (!o->core || !o->cid || !o->label)) { set_error("NULL output array"); return SCAN_EINVAL; }
     if (!o->npairs || (o->pairs_cap > 0 && !o->pairs) || o->pairs_cap < 0) {
         set_error("bad pairs output");
@@ -380,6 +401,7 @@ scan_status scan_query_ex(scan_graph *g, const scan_params *params, uint32_t mod
     SCAN_TRY(check_params(params));
     Ctx *c = g->ctx;
     SCAN_CUDA(cudaSetDevice(c->device));
+    if (g->part) return part_query(g, *params, out);  // every mode is a full recompute out of core
     auto *core = (uint8_t *)g->core.ptr;
     auto *cid = (int32_t *)g->cid.ptr;
     auto *label = (uint8_t *)g->label.ptr;

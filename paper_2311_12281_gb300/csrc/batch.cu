@@ -269,10 +269,12 @@ scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t 
 
 scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs) {
     try {
-        if (!gs || !params || !outs || k < 1) { set_error("bad arguments"); return SCAN_EINVAL; }
+        if (!gs || !params || !outs || k < 1 || !gs[0]) { set_error("bad arguments"); return SCAN_EINVAL; }
         Ctx *c = gs[0]->ctx;
-        for (int32_t j = 0; j < k; ++j)
+        for (int32_t j = 0; j < k; ++j) {
             if (!gs[j] || gs[j]->ctx != c) { set_error("all graphs of a batch must share one context"); return SCAN_EINVAL; }
+            if (gs[j]->part) { set_error("a partitioned graph cannot join a batch"); return SCAN_EINVAL; }
+        }
         SCAN_CUDA(cudaSetDevice(c->device));
         // bring every graph's CSR back to the host and build the union
         std::vector<std::vector<int64_t>> offs((size_t)k);

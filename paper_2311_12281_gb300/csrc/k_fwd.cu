@@ -23,11 +23,10 @@ namespace scan {
 namespace {
 
 constexpr int kFwdSmallOut = 64;         // warp-level owners: out-degree bound
-constexpr int64_t kFwdSmallWork = 1 << 15;  // ... and probe bound
 constexpr int kFwdSmallTable = 256;      // slots per warp table
 constexpr int kFwdChunk = 4096;          // max out(b) elements per CTA table
-constexpr int64_t kFwdItemWork = 1 << 20;  // target probes per CTA item
-constexpr int kFwdPiece = 256;
+// (the warp-owner probe bound and the probes per CTA item are per-graph
+// schedule parameters: Graph::fwd_small_work, Graph::fwd_item_work)
 constexpr int kFwdUnroll = 8;
 constexpr unsigned long long kSlotEmpty = ~0ull;
 
@@ -235,24 +234,62 @@ __device__ __forceinline__ T fblock_scan(T x, T *total, T *wsum) {
     return ex;
 }
 
+// Table of the CTA owners: buckets of two (key, count) pairs, 16 bytes, so
+// one 128-bit shared-memory load answers most lookups. A key goes to the
+// first bucket, from its hash on, with a free pair; a bucket whose second
+// key is empty never overflowed, which ends a lookup. Empty key: -1.
+__device__ __forceinline__ void btab_insert(int4 *tab, int lognb, int32_t key) {
+    const uint32_t mask = (1u << lognb) - 1u;
+    uint32_t h = fhash(key, lognb);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        int *w = (int *)(tab + h);
+        if (atomicCAS(w + 0, -1, key) == -1) return;
+        if (atomicCAS(w + 2, -1, key) == -1) return;
+        h = (h + 1) & mask;
+    }
+}
+
+// index (in ints) of key's count word, or -1
+__device__ __forceinline__ int32_t btab_find(const int4 *tab, int lognb, int32_t key) {
+    const uint32_t mask = (1u << lognb) - 1u;
+    uint32_t h = fhash(key, lognb);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const int4 b = tab[h];
+        if (b.x == key) return (int32_t)(4 * h + 1);
+        if (b.z == key) return (int32_t)(4 * h + 3);
+        if (b.z == -1) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+constexpr int kStepsPerGroup = 4;  // 32-position steps whose loads are issued together
+
 // One CTA per item (owner b, value chunk of out(b), slot range of b's row).
-// Dynamic shared memory: the table (cap 64-bit slots) then the per-owner
-// counters (kFwdChunk ints).
+// The rows of b are taken BLOCK at a time. Each in-neighbour a of such a
+// round with something to stream contributes an entry: the part of out(a)
+// that can close a triangle a < b < c. The entries are compacted and their
+// lengths prefix-summed into one flat range of probe positions, which the
+// warps split evenly. A warp walks its share 32 consecutive positions per
+// step, lane l on position q0 + l: the entries starting inside the step are
+// found with one shared-memory load per lane and a warp-wide OR of their
+// offsets, so the walk is uniform however short or long the entries are.
+// A hit c adds one to (b, c) in the table, to (a, c) at the streamed slot in
+// global memory, and to (a, b) through the entry's shared counter.
+// Dynamic shared memory: 2^cap_lognb buckets.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ items, const int64_t *__restrict__ off,
                                                    const int32_t *__restrict__ adj, const int32_t *__restrict__ deg,
                                                    const int64_t *__restrict__ foff, const int32_t *__restrict__ fadj,
                                                    const uint32_t *__restrict__ fin, int32_t *__restrict__ fcnt,
-                                                   int cap_log, int cap_logb, int rank_sorted) {
-    extern __shared__ unsigned long long t[];
-    uint32_t *bm = (uint32_t *)(t + (1 << cap_log));
-    int32_t *ocnt = (int32_t *)(bm + (1 << (cap_logb - 5)));
-    __shared__ int32_t w_s[BLOCK], w_start[BLOCK], w_len[BLOCK], w_cnt[BLOCK];
-    __shared__ int64_t w_fa[BLOCK];
-    __shared__ int32_t l_idx[BLOCK], l_poff[BLOCK + 1], s_idx[BLOCK];
-    __shared__ long long wsum64[BLOCK / 32 + 1];
-    __shared__ int32_t wsum32[BLOCK / 32 + 1];
-    __shared__ int32_t piece_ctr, short_ctr;
+                                                   int cap_lognb, int load_shift, int rank_sorted) {
+    extern __shared__ int4 btab[];
+    int *tword = (int *)btab;
+    __shared__ int32_t c_pos[BLOCK + 1];   // flat start of each compacted entry; c_pos[nwork] = total
+    __shared__ int32_t c_base[BLOCK + 1];  // fadj index of an entry's first id, minus its flat start
+    __shared__ uint32_t c_fin[BLOCK];      // fcnt index of the entry's edge (a, b)
+    __shared__ int32_t e_cnt[BLOCK];       // triangles found per entry
+    __shared__ long long wsum[BLOCK / 32 + 1];
 
     const FItem it = items[blockIdx.x];
     const int32_t b = it.v;
@@ -265,24 +302,22 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
     const int32_t hi = te == ob ? INT32_MAX : fadj[fb + te];
     const unsigned long long lo_key = tb == 0 ? 0ull : rank_key(deg, lo);
     const unsigned long long hi_key = te == ob ? ~0ull : rank_key(deg, hi);
-    const int logc = min(cap_log, max(5, fceil_log2(4 * tlen)));
-    const int logb = min(cap_logb, max(5, fceil_log2(32 * tlen)));
-    for (int k = threadIdx.x; k < (1 << logc); k += BLOCK) t[k] = kSlotEmpty;
-    for (int k = threadIdx.x; k < (1 << (logb - 5)); k += BLOCK) bm[k] = 0u;
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) ocnt[k] = 0;
+    // buckets: 2^load_shift per key (two pairs each), at most 2^cap_lognb
+    const int lognb = min(cap_lognb, max(4, fceil_log2(tlen << load_shift)));
+    for (int k = threadIdx.x; k < (1 << lognb); k += BLOCK) btab[k] = make_int4(-1, 0, -1, 0);
     __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
-        const int32_t x = fadj[fb + tb + k];
-        ftab_insert(t, logc, x, k);
-        fbits_set(bm, logb, x);
-    }
-    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) btab_insert(btab, lognb, fadj[fb + tb + k]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned le_mask = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+    constexpr long long kIdx = 1ll << 40;
 
     for (int32_t r0 = it.sb; r0 < it.se; r0 += BLOCK) {
         const int32_t rel = r0 + threadIdx.x;
         bool work = false;
-        int32_t start = 0, len = 0, s32 = 0;
+        int32_t start = 0, len = 0;
         int64_t fa = 0;
+        uint32_t fab = 0;
         if (rel < it.se) {
             const int64_t s = rb + rel;
             const int32_t a = adj[s], da = deg[a];
@@ -291,9 +326,10 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
                 const int32_t oa = (int32_t)(foff[a + 1] - fa);
                 const int32_t *row = fadj + fa;
                 int32_t end = oa;
+                fab = fin[s];
                 if (rank_sorted) {
                     // common neighbours of a and b rank above b: the suffix after b
-                    start = (int32_t)((int64_t)fin[s] - fa) + 1;
+                    start = (int32_t)((int64_t)fab - fa) + 1;
                     if (chunked) {
                         start = max(start, rank_lower_bound(row, oa, deg, lo_key));
                         end = hi_key == ~0ull ? oa : rank_lower_bound(row, oa, deg, hi_key);
@@ -302,83 +338,87 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
                     start = lo == INT32_MIN ? 0 : lower_bound_row(row, oa, lo);
                     end = hi == INT32_MAX ? oa : lower_bound_row(row, oa, hi);
                 }
-                len = end - start;
+                len = max(end - start, 0);
                 work = len > 0;
-                s32 = rel;
             }
         }
-        const bool is_long = work && len >= kWarp;
-        const bool is_short = work && len < kWarp;
-        const long long flags = (long long)work | ((long long)is_long << 21) | ((long long)is_short << 42);
+        // one scan: compacted index in the high bits, flat position in the low 40
         long long tot;
-        const long long ex = fblock_scan<BLOCK, long long>(flags, &tot, wsum64);
-        int32_t tot_pieces;
-        const int32_t pex = fblock_scan<BLOCK, int32_t>(is_long ? (len + kFwdPiece - 1) / kFwdPiece : 0, &tot_pieces,
-                                                        wsum32);
-        const int32_t n_work = (int32_t)(tot & 0x1FFFFF);
-        const int32_t n_long = (int32_t)((tot >> 21) & 0x1FFFFF);
-        const int32_t n_short = (int32_t)((tot >> 42) & 0x1FFFFF);
+        const long long ex = fblock_scan<BLOCK, long long>(work ? kIdx + len : 0ll, &tot, wsum);
+        const int32_t nwork = (int32_t)(tot >> 40), total = (int32_t)(tot & (kIdx - 1));
         if (work) {
-            const int32_t e = (int32_t)(ex & 0x1FFFFF);
-            w_s[e] = s32;
-            w_fa[e] = fa;
-            w_start[e] = start;
-            w_len[e] = len;
-            w_cnt[e] = 0;
-            if (is_long) {
-                const int32_t l = (int32_t)((ex >> 21) & 0x1FFFFF);
-                l_idx[l] = e;
-                l_poff[l] = pex;
-            }
-            if (is_short) s_idx[(ex >> 42) & 0x1FFFFF] = e;
+            const int32_t k = (int32_t)(ex >> 40), pos = (int32_t)(ex & (kIdx - 1));
+            c_pos[k] = pos;
+            c_base[k] = (int32_t)(fa + start - pos);  // fadj indices are < m < 2^31
+            c_fin[k] = fab;
+            e_cnt[k] = 0;
         }
         if (threadIdx.x == 0) {
-            l_poff[n_long] = tot_pieces;
-            piece_ctr = 0;
-            short_ctr = 0;
+            c_pos[nwork] = total;
+            c_base[nwork] = 0;
         }
         __syncthreads();
-        for (int guard = 0; guard < (1 << 30); ++guard) {
-            int32_t p = 0;
-            if (lane == 0) p = atomicAdd(&piece_ctr, 1);
-            p = __shfl_sync(0xffffffffu, p, 0);
-            if (p >= tot_pieces) break;
-            int32_t li = 0, hi_i = n_long;
-            while (hi_i - li > 1) {
-                const int32_t mid = (li + hi_i) >> 1;
-                if (l_poff[mid] <= p) li = mid;
-                else hi_i = mid;
+        // this warp's share of [0, total), in whole steps
+        const int32_t share = (((total + BLOCK / 32 - 1) / (BLOCK / 32)) + 31) & ~31;
+        const int32_t q_begin = warp * share, q_end = min(total, q_begin + share);
+        if (q_begin < q_end) {
+            // entry holding q_begin: the last e with c_pos[e] <= q_begin
+            int32_t el = 0, eh = nwork;
+            while (eh - el > 1) {
+                const int32_t mid = (el + eh) >> 1;
+                if (c_pos[mid] <= q_begin) el = mid;
+                else eh = mid;
             }
-            const int32_t e = l_idx[li];
-            const int32_t o = w_start[e] + (p - l_poff[li]) * kFwdPiece;
-            const int32_t pend = min(o + kFwdPiece, w_start[e] + w_len[e]);
-            const int64_t fa = w_fa[e];
-            int c = probe_run<kFwdUnroll>(fadj + fa, fcnt + fa, o + lane, pend, kWarp, t, logc, bm, logb, ocnt);
-            c = __reduce_add_sync(0xffffffffu, c);
-            if (lane == 0 && c) atomicAdd(&w_cnt[e], c);
-        }
-        for (int guard = 0; guard < (1 << 30); ++guard) {
-            int32_t q = 0;
-            if (lane == 0) q = atomicAdd(&short_ctr, kWarp);
-            q = __shfl_sync(0xffffffffu, q, 0);
-            if (q >= n_short) break;
-            const int32_t k = q + lane;
-            if (k < n_short) {
-                const int32_t e = s_idx[k];
-                const int64_t fa = w_fa[e];
-                w_cnt[e] = probe_run<4>(fadj + fa, fcnt + fa, w_start[e], w_start[e] + w_len[e], 1, t, logc, bm,
-                                        logb, ocnt);
+            int32_t e0 = el;  // entry of the current step's first position
+            for (int32_t g0 = q_begin; g0 < q_end; g0 += 32 * kStepsPerGroup) {
+                int32_t aj[kStepsPerGroup], ej[kStepsPerGroup];
+                unsigned mj[kStepsPerGroup];
+#pragma unroll
+                for (int u = 0; u < kStepsPerGroup; ++u) {
+                    const int32_t qs = g0 + 32 * u;
+                    // entries starting inside this step (offsets 1..31) or at the next one (32)
+                    const int32_t bk = c_pos[min(e0 + 1 + lane, nwork)];
+                    const int32_t d = bk - qs;
+                    const unsigned m = __reduce_or_sync(0xffffffffu, (d > 0 && d < 32) ? (1u << d) : 0u);
+                    const int32_t e = e0 + __popc(m & le_mask);
+                    const int32_t q = qs + lane;
+                    ej[u] = e;
+                    mj[u] = m;
+                    aj[u] = q < q_end ? c_base[e] + q : -1;
+                    e0 += __popc(m) + (__any_sync(0xffffffffu, d == 32) ? 1 : 0);
+                }
+                int32_t xj[kStepsPerGroup];
+#pragma unroll
+                for (int u = 0; u < kStepsPerGroup; ++u) xj[u] = aj[u] >= 0 ? __ldg(fadj + aj[u]) : -1;
+#pragma unroll
+                for (int u = 0; u < kStepsPerGroup; ++u) {
+                    bool hit = false;
+                    if (aj[u] >= 0) {
+                        const int32_t w = btab_find(btab, lognb, xj[u]);
+                        if (w >= 0) {
+                            hit = true;
+                            atomicAdd(tword + w, 1);       // edge (b, c)
+                            atomicAdd(fcnt + aj[u], 1);    // edge (a, c)
+                        }
+                    }
+                    // edge (a, b): one add per step when the step lies in one entry
+                    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                    if (mj[u] == 0) {
+                        if (lane == 0 && hm) atomicAdd(&e_cnt[ej[u]], __popc(hm));
+                    } else if (hit) {
+                        atomicAdd(&e_cnt[ej[u]], 1);
+                    }
+                }
             }
         }
         __syncthreads();
-        if (threadIdx.x < n_work) {
-            const int32_t e = threadIdx.x;
-            if (w_cnt[e]) atomicAdd(fcnt + fin[rb + w_s[e]], w_cnt[e]);
-        }
+        if (threadIdx.x < nwork && e_cnt[threadIdx.x]) atomicAdd(fcnt + c_fin[threadIdx.x], e_cnt[threadIdx.x]);
         __syncthreads();
     }
-    for (int k = threadIdx.x; k < tlen; k += BLOCK)
-        if (ocnt[k]) atomicAdd(fcnt + fb + tb + k, ocnt[k]);
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+        const int32_t w = btab_find(btab, lognb, fadj[fb + tb + k]);
+        if (w >= 0 && tword[w]) atomicAdd(fcnt + fb + tb + k, tword[w]);
+    }
 }
 
 // per forward edge: closed count, mirrored to both slots; optional eps-test
@@ -509,7 +549,8 @@ __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restri
                                                          const int32_t *__restrict__ deg,
                                                          const int64_t *__restrict__ foff, int32_t n,
                                                          int32_t *__restrict__ nranges,
-                                                         unsigned long long *counts) {
+                                                         unsigned long long *counts, int64_t small_work,
+                                                         int64_t item_work) {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
     const int lane = threadIdx.x & 31;
     if (b >= n) return;
@@ -525,13 +566,13 @@ __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restri
     }
     for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (lane != 0 || w == 0) return;
-    if (ob <= kFwdSmallOut && (int64_t)w <= kFwdSmallWork) {
+    if (ob <= kFwdSmallOut && (int64_t)w <= small_work) {
         nranges[b] = -1;  // warp owner
         atomicAdd(counts + 0, 1ull);
         return;
     }
     const int64_t nchunks = (ob + kFwdChunk - 1) / kFwdChunk;
-    int64_t nr = (int64_t)((w + kFwdItemWork - 1) / kFwdItemWork);
+    int64_t nr = (int64_t)((w + item_work - 1) / item_work);
     nr = max((int64_t)1, min(nr, (int64_t)(db + 255) / 256));
     nranges[b] = (int32_t)nr;
     atomicAdd(counts + (ob <= 1024 ? 1 : 2), (unsigned long long)(nchunks * nr));
@@ -569,19 +610,26 @@ scan_status fwd_prepare(Graph *g) {
         g->fwd_ready = true;
         return SCAN_OK;
     }
-    SCAN_TRY(dev_alloc(c, g->fadj, 4 * (size_t)m));
-    SCAN_TRY(dev_alloc(c, g->fin, 4 * (size_t)g->nnz));
-    SCAN_TRY(dev_alloc(c, g->fcnt, 4 * (size_t)m));
-    // foff (built at load) already holds the out-degree offsets
-    k_fwd_adj<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
-        (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->adj.ptr, (const uint32_t *)g->rev.ptr,
-        (int32_t *)g->fadj.ptr, (uint32_t *)g->fin.ptr);
-    c->launches++;
     DevBuf cnts;
     SCAN_TRY(dev_alloc(c, cnts, 4 * sizeof(unsigned long long)));
     auto *counts = (unsigned long long *)cnts.ptr;
-    // order every out-list by rank, carrying the slot ids, then re-index fin
-    {
+    if (!g->fadj.ptr) {
+        scan_status s = dev_alloc(c, g->fadj, 4 * (size_t)m);
+        if (s == SCAN_OK) s = dev_alloc(c, g->fin, 4 * (size_t)g->nnz);
+        if (s == SCAN_OK) s = dev_alloc(c, g->fcnt, 4 * (size_t)m);
+        if (s != SCAN_OK) {
+            dev_free(c, g->fadj);
+            dev_free(c, g->fin);
+            dev_free(c, g->fcnt);
+            dev_free(c, cnts);
+            return s;
+        }
+        // foff (built at load) already holds the out-degree offsets
+        k_fwd_adj<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
+            (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->adj.ptr, (const uint32_t *)g->rev.ptr,
+            (int32_t *)g->fadj.ptr, (uint32_t *)g->fin.ptr);
+        c->launches++;
+        // order every out-list by rank, carrying the slot ids, then re-index fin
         SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
         int32_t *verts = (int32_t *)g->cnt.ptr;  // scratch int32[n+1]
         k_fwd_sort_pick<<<grid_for(n, 256), 256, 0, c->stream>>>((const int64_t *)g->foff.ptr, n, verts, counts);
@@ -603,12 +651,12 @@ scan_status fwd_prepare(Graph *g) {
             c->launches += 2 + (h2[0] > 0);
         }
     }
-    // schedule
+    // schedule (rebuilt alone when the autotuner changes its parameters)
     SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
     int32_t *nranges = (int32_t *)g->ucnt.ptr;  // scratch int32[n+1]
     k_fwd_sched_count<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(
         (const int64_t *)g->off.ptr, (const int32_t *)g->adj.ptr, (const int32_t *)g->deg.ptr,
-        (const int64_t *)g->foff.ptr, n, nranges, counts);
+        (const int64_t *)g->foff.ptr, n, nranges, counts, g->fwd_small_work, g->fwd_item_work);
     c->launches++;
     unsigned long long h[4];
     SCAN_CUDA(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -650,22 +698,16 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     auto *fcnt = (int32_t *)g->fcnt.ptr;
     SCAN_CUDA(cudaMemsetAsync(fcnt, 0, 4 * (size_t)g->m, st));
     const int rs = g->fwd_rank_sorted ? 1 : 0;
-    if (g->fwd_items_n[2] > 0) {  // out-degree > 1024: 16384-slot tables, 2^17-bit filters
-        const int cap_log = 14, cap_logb = 17;
-        const size_t smem = (8u << cap_log) + (1u << (cap_logb - 3)) + 4 * kFwdChunk;
-        auto kern = k_fwd_cta<512>;
+    auto kern = k_fwd_cta<512>;
+    for (int cls = 2; cls >= 1; --cls) {
+        if (g->fwd_items_n[cls] == 0) continue;
+        // class 1 (out-degree <= 1024): 4 buckets per key, up to 4096 (64 KB);
+        // class 2 (chunks of up to 4096 keys): 2 buckets per key, up to 8192 (128 KB)
+        const int cap_lognb = cls == 2 ? 13 : 12, load_shift = cls == 2 ? 1 : 2;
+        const size_t smem = sizeof(int4) << cap_lognb;
         SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)g->fwd_items_n[2], 512, smem, st>>>((const FItem *)g->fwd_items[2].ptr, off, adj, deg, foff,
-                                                           fadj, fin, fcnt, cap_log, cap_logb, rs);
-        c->launches++;
-    }
-    if (g->fwd_items_n[1] > 0) {  // out-degree <= 1024: 4096-slot tables, 2^15-bit filters
-        const int cap_log = 12, cap_logb = 15;
-        const size_t smem = (8u << cap_log) + (1u << (cap_logb - 3)) + 4 * 1024;
-        auto kern = k_fwd_cta<512>;
-        SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)g->fwd_items_n[1], 512, smem, st>>>((const FItem *)g->fwd_items[1].ptr, off, adj, deg, foff,
-                                                           fadj, fin, fcnt, cap_log, cap_logb, rs);
+        kern<<<(unsigned)g->fwd_items_n[cls], 512, smem, st>>>((const FItem *)g->fwd_items[cls].ptr, off, adj, deg,
+                                                             foff, fadj, fin, fcnt, cap_lognb, load_shift, rs);
         c->launches++;
     }
     if (g->fwd_small > 0) {

@@ -89,21 +89,89 @@ __global__ void __launch_bounds__(kBlock) k_sim_from_counts(
 }
 
 // ------------------------------------------------------------------ cores
-// Warp per vertex: count similar slots, stop once 1 + count >= mu.
+// Rows of at most kCoop slots are walked by one thread; longer rows by the
+// whole warp (each warp gathers its threads' long rows and takes them in
+// turn). Most vertices of a power-law graph have short rows, so a warp keeps
+// 32 independent load chains in flight instead of one.
+constexpr int kCoop = 32;
+
+// Rows longer than kHeavy slots belong to the heavy list and are walked by a
+// whole CTA each (the *_heavy kernels below); the per-vertex kernels skip them.
+constexpr int kHeavy = 1024;
+
+// |N_eps[u]| = 1 + similar slots of row u; counting stops once it reaches mu.
 __global__ void __launch_bounds__(kBlock) k_core(const int64_t *__restrict__ off, const uint8_t *__restrict__ sim,
                                                  int32_t n, QParams qp, uint8_t *__restrict__ core) {
-    const int64_t u = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;
+    const int64_t u = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (u >= n) return;
-    const uint32_t mu = qp.mu_of((int32_t)u);
-    const int64_t b = off[u], e = off[u + 1];
-    uint32_t cnt = 1;  // u itself: sigma(u, u) = 1
-    for (int64_t s0 = b; s0 < e && cnt < mu; s0 += kWarp) {
-        const int64_t s = s0 + lane;
-        const bool hit = s < e && sim[s];
-        cnt += __popc(__ballot_sync(0xffffffffu, hit));
+    int64_t b = 0, e = 0;
+    uint32_t mu = 0;
+    bool mine = false;  // rows above kHeavy are the heavy kernel's
+    if (u < n) {
+        b = off[u];
+        e = off[u + 1];
+        mu = qp.mu_of((int32_t)u);
+        mine = e - b <= kHeavy;
     }
-    if (lane == 0) core[u] = cnt >= mu ? 1 : 0;
+    const bool heavy = mine && e - b > kCoop;
+    if (mine && !heavy) {
+        uint32_t cnt = 1;  // u itself: sigma(u, u) = 1
+        for (int64_t s = b; s < e && cnt < mu; s += 4) {
+            uint32_t x = sim[s];
+            if (s + 1 < e) x += sim[s + 1];
+            if (s + 2 < e) x += sim[s + 2];
+            if (s + 3 < e) x += sim[s + 3];
+            cnt += x;
+        }
+        core[u] = cnt >= mu ? 1 : 0;
+    }
+    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
+        const int src = __ffs(hv) - 1;
+        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+        const uint32_t hmu = __shfl_sync(0xffffffffu, mu, src);
+        uint32_t cnt = 1;
+        for (int64_t s0 = hb; s0 < he && cnt < hmu; s0 += 4 * kWarp) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t s = s0 + j * kWarp + lane;
+                x += (s < he && sim[s]) ? 1u : 0u;
+            }
+            cnt += __reduce_add_sync(0xffffffffu, x);
+        }
+        if (lane == src) core[u] = cnt >= hmu ? 1 : 0;
+    }
+}
+
+// ------------------------------------------------------------------ heavy rows
+// Block-wide sum / min / max / or of one int per thread (all threads call).
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T x, Op op, T *red) {
+    for (int o = 16; o; o >>= 1) x = op(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    T y = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) y = op(y, red[w]);
+    return y;
+}
+
+struct OpAdd { __device__ int operator()(int a, int b) const { return a + b; } };
+struct OpMin { __device__ int operator()(int a, int b) const { return min(a, b); } };
+struct OpMax { __device__ int operator()(int a, int b) const { return max(a, b); } };
+
+// CTA per heavy vertex: |N_eps[u]| over the whole row.
+__global__ void __launch_bounds__(kBlock) k_core_heavy(const int32_t *__restrict__ heavy, const int64_t *__restrict__ off,
+                                                       const uint8_t *__restrict__ sim, QParams qp,
+                                                       uint8_t *__restrict__ core) {
+    __shared__ int red[kBlock / 32];
+    const int32_t u = heavy[blockIdx.x];
+    const int64_t b = off[u], e = off[u + 1];
+    int c = 0;
+    for (int64_t s = b + threadIdx.x; s < e; s += kBlock) c += sim[s];
+    c = block_reduce(c, OpAdd(), red);
+    if (threadIdx.x == 0) core[u] = (uint32_t)c + 1u >= qp.mu_of(u) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ union-find
@@ -158,68 +226,176 @@ __global__ void k_uf_final(const uint8_t *__restrict__ core, int32_t n, int32_t 
 }
 
 // ------------------------------------------------------------------ borders
-// Warp per non-core vertex: number of eps-similar core neighbours (< mu - 1).
+// Membership code memb[v] (the parent array after union-find): a core's cid;
+// for a border vertex its only cluster id, or kMulti when it belongs to two
+// or more clusters; -1 for a vertex in no cluster.
+constexpr int32_t kMulti = -2;
+
+// Per non-core vertex: number of eps-similar core neighbours (< mu - 1).
+// Also starts every vertex's membership code from its cid (-1 off cores);
+// union-find is finished, so the parent array is free to hold it.
 __global__ void __launch_bounds__(kBlock) k_border_count(const int64_t *__restrict__ off,
                                                         const int32_t *__restrict__ adj,
                                                         const uint8_t *__restrict__ sim,
-                                                        const uint8_t *__restrict__ core, int32_t n,
-                                                        int32_t *__restrict__ cnt) {
-    const int64_t v = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;
+                                                        const uint8_t *__restrict__ core,
+                                                        const int32_t *__restrict__ cid, int32_t *__restrict__ memb,
+                                                        int32_t n, int32_t *__restrict__ cnt) {
+    const int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (v >= n) return;
-    int c = 0;
-    if (!core[v]) {
-        const int64_t b = off[v], e = off[v + 1];
-        for (int64_t s = b + lane; s < e; s += kWarp) c += (sim[s] && core[adj[s]]) ? 1 : 0;
-        c = __reduce_add_sync(0xffffffffu, c);
+    int64_t b = 0, e = 0;
+    bool mine = false;  // rows above kHeavy are the heavy kernel's
+    if (v < n) {
+        memb[v] = cid[v];
+        b = off[v];
+        e = off[v + 1];
+        mine = e - b <= kHeavy;
+        if (core[v]) e = b;  // a core has no border candidates
     }
-    if (lane == 0) cnt[v] = c;
+    const bool heavy = mine && e - b > kCoop;
+    if (mine && !heavy) {
+        int c = 0;
+        for (int64_t s = b; s < e; ++s)
+            if (sim[s]) c += core[adj[s]];
+        cnt[v] = c;
+    }
+    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
+        const int src = __ffs(hv) - 1;
+        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+        int c = 0;
+        for (int64_t s = hb + lane; s < he; s += kWarp)
+            if (sim[s]) c += core[adj[s]];
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == src) cnt[v] = c;
+    }
 }
 
-// Warp per non-core vertex: write the candidate cluster ids, then lane 0
-// sorts the (short) segment and removes duplicates.
-__global__ void __launch_bounds__(kBlock) k_border_fill(const int64_t *__restrict__ off,
-                                                       const int32_t *__restrict__ adj,
-                                                       const uint8_t *__restrict__ sim,
-                                                       const uint8_t *__restrict__ core,
-                                                       const int32_t *__restrict__ cid, int32_t n,
-                                                       const int64_t *__restrict__ raw_off, int32_t *__restrict__ raw,
-                                                       int32_t *__restrict__ ucnt) {
-    const int64_t v = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;
-    const int lane = threadIdx.x & 31;
-    if (v >= n) return;
-    const int64_t base = raw_off[v], k = raw_off[v + 1] - base;
-    if (k == 0) {
-        if (lane == 0) ucnt[v] = 0;
+// CTA per heavy vertex: its border candidate count.
+__global__ void __launch_bounds__(kBlock) k_border_count_heavy(const int32_t *__restrict__ heavy,
+                                                              const int64_t *__restrict__ off,
+                                                              const int32_t *__restrict__ adj,
+                                                              const uint8_t *__restrict__ sim,
+                                                              const uint8_t *__restrict__ core,
+                                                              int32_t *__restrict__ cnt) {
+    __shared__ int red[kBlock / 32];
+    const int32_t v = heavy[blockIdx.x];
+    if (core[v]) {
+        if (threadIdx.x == 0) cnt[v] = 0;
         return;
     }
     const int64_t b = off[v], e = off[v + 1];
-    int64_t w = base;
-    for (int64_t s0 = b; s0 < e; s0 += kWarp) {
-        const int64_t s = s0 + lane;
-        int32_t x = -1;
-        bool f = false;
-        if (s < e && sim[s]) {
-            const int32_t u = adj[s];
-            if (core[u]) { f = true; x = cid[u]; }
+    int c = 0;
+    for (int64_t s = b + threadIdx.x; s < e; s += kBlock)
+        if (sim[s]) c += core[adj[s]];
+    c = block_reduce(c, OpAdd(), red);
+    if (threadIdx.x == 0) cnt[v] = c;
+}
+
+// Sorts a[0, k) (k < mu - 1, short) and removes duplicates; returns the
+// number of distinct values.
+__device__ __forceinline__ int32_t sort_unique(int32_t *a, int64_t k) {
+    for (int64_t i = 1; i < k; ++i) {
+        const int32_t t = a[i];
+        int64_t j = i - 1;
+        while (j >= 0 && a[j] > t) {
+            a[j + 1] = a[j];
+            --j;
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, f);
-        if (f) raw[w + __popc(mask & ((1u << lane) - 1u))] = x;
-        w += __popc(mask);
+        a[j + 1] = t;
     }
-    __syncwarp();
-    if (lane == 0) {
-        int32_t *a = raw + base;
-        for (int64_t i = 1; i < k; ++i) {  // insertion sort: k < mu - 1
-            int32_t t = a[i];
-            int64_t j = i - 1;
-            while (j >= 0 && a[j] > t) { a[j + 1] = a[j]; --j; }
-            a[j + 1] = t;
+    int64_t u = 1;
+    for (int64_t i = 1; i < k; ++i)
+        if (a[i] != a[u - 1]) a[u++] = a[i];
+    return (int32_t)u;
+}
+
+// Per vertex with candidates: the cluster ids of its eps-similar core
+// neighbours, sorted and unique, and its membership code.
+__global__ void __launch_bounds__(kBlock) k_border_fill(const int64_t *__restrict__ off,
+                                                       const int32_t *__restrict__ adj,
+                                                       const uint8_t *__restrict__ sim,
+                                                       const uint8_t *__restrict__ core, int32_t *memb, int32_t n,
+                                                       const int64_t *__restrict__ raw_off, int32_t *__restrict__ raw,
+                                                       int32_t *__restrict__ ucnt) {
+    const int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int64_t b = 0, e = 0, base = 0, k = 0;
+    if (v < n) {
+        base = raw_off[v];
+        k = raw_off[v + 1] - base;
+        if (k > 0) {
+            b = off[v];
+            e = off[v + 1];
+            if (e - b > kHeavy) k = 0, b = e = 0;  // the heavy kernel's
+        } else {
+            ucnt[v] = 0;
         }
-        int64_t u = 1;
-        for (int64_t i = 1; i < k; ++i)
-            if (a[i] != a[u - 1]) a[u++] = a[i];
-        ucnt[v] = (int32_t)u;
+    }
+    const bool heavy = e - b > kCoop;
+    if (k > 0 && !heavy) {
+        int64_t w = base;
+        for (int64_t s = b; s < e; ++s)
+            if (sim[s]) {
+                const int32_t x = adj[s];
+                if (core[x]) raw[w++] = memb[x];  // x is a core: memb is its cid
+            }
+        const int32_t uq = sort_unique(raw + base, k);
+        ucnt[v] = uq;
+        memb[v] = uq == 1 ? raw[base] : kMulti;
+    }
+    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
+        const int src = __ffs(hv) - 1;
+        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+        int64_t w = __shfl_sync(0xffffffffu, base, src);
+        for (int64_t s0 = hb; s0 < he; s0 += kWarp) {
+            const int64_t s = s0 + lane;
+            int32_t x = -1;
+            bool f = false;
+            if (s < he && sim[s]) {
+                const int32_t y = adj[s];
+                if (core[y]) {
+                    f = true;
+                    x = memb[y];
+                }
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, f);
+            if (f) raw[w + __popc(mask & ((1u << lane) - 1u))] = x;
+            w += __popc(mask);
+        }
+        __syncwarp();
+        if (lane == src) {
+            const int32_t uq = sort_unique(raw + base, k);
+            ucnt[v] = uq;
+            memb[v] = uq == 1 ? raw[base] : kMulti;
+        }
+        __syncwarp();
+    }
+}
+
+// CTA per heavy vertex with candidates: gathered in any order, then sorted.
+__global__ void __launch_bounds__(kBlock) k_border_fill_heavy(const int32_t *__restrict__ heavy,
+                                                             const int64_t *__restrict__ off,
+                                                             const int32_t *__restrict__ adj,
+                                                             const uint8_t *__restrict__ sim,
+                                                             const uint8_t *__restrict__ core, int32_t *memb,
+                                                             const int64_t *__restrict__ raw_off,
+                                                             int32_t *__restrict__ raw, int32_t *__restrict__ ucnt) {
+    __shared__ int32_t fill;
+    const int32_t v = heavy[blockIdx.x];
+    const int64_t base = raw_off[v], k = raw_off[v + 1] - base;
+    if (k == 0) return;  // ucnt[v] = 0 was written by the per-vertex kernel
+    if (threadIdx.x == 0) fill = 0;
+    __syncthreads();
+    const int64_t b = off[v], e = off[v + 1];
+    for (int64_t s = b + threadIdx.x; s < e; s += kBlock)
+        if (sim[s]) {
+            const int32_t y = adj[s];
+            if (core[y]) raw[base + atomicAdd(&fill, 1)] = memb[y];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t uq = sort_unique(raw + base, k);
+        ucnt[v] = uq;
+        memb[v] = uq == 1 ? raw[base] : kMulti;
     }
 }
 
@@ -238,46 +414,150 @@ __global__ void k_border_emit(const int64_t *__restrict__ raw_off, const int32_t
 }
 
 // ------------------------------------------------------------------ labels
-// Warp per vertex. A vertex in no cluster is a hub iff the union of its
-// neighbours' memberships holds two distinct ids: some neighbour is itself
-// in >= 2 clusters, or two neighbours' single ids differ (min != max).
+// A vertex in no cluster is a hub iff the union of its neighbours'
+// memberships holds two distinct ids: some neighbour is itself in two or
+// more clusters (kMulti), or two neighbours' single ids differ.
 __global__ void __launch_bounds__(kBlock) k_label(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                                                 const uint8_t *__restrict__ core, const int32_t *__restrict__ cid,
-                                                 const int32_t *__restrict__ ucnt, const int64_t *__restrict__ raw_off,
-                                                 const int32_t *__restrict__ raw, int32_t n,
-                                                 uint8_t *__restrict__ label) {
-    const int64_t u = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;
+                                                 const uint8_t *__restrict__ core, const int32_t *__restrict__ memb,
+                                                 int32_t n, uint8_t *__restrict__ label) {
+    const int64_t u = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (u >= n) return;
-    if (core[u]) { if (lane == 0) label[u] = SCAN_CORE; return; }
-    if (ucnt[u] > 0) { if (lane == 0) label[u] = SCAN_BORDER; return; }
-    const int64_t b = off[u], e = off[u + 1];
-    int32_t lo = INT32_MAX, hi = -1;
-    bool multi = false;
-    for (int64_t s0 = b; s0 < e; s0 += kWarp) {
-        const int64_t s = s0 + lane;
-        if (s < e) {
-            const int32_t w = adj[s];
-            int32_t id = -1;
-            if (core[w]) id = cid[w];
-            else if (ucnt[w] > 0) {
-                id = raw[raw_off[w]];
-                multi |= ucnt[w] > 1;
-            }
-            if (id >= 0) { lo = min(lo, id); hi = max(hi, id); }
-        }
-        const bool any_multi = __any_sync(0xffffffffu, multi);
-        const int32_t glo = __reduce_min_sync(0xffffffffu, lo);
-        const int32_t ghi = __reduce_max_sync(0xffffffffu, hi);
-        if (any_multi || (ghi >= 0 && glo != ghi)) {
-            if (lane == 0) label[u] = SCAN_HUB;
-            return;
+    int64_t b = 0, e = 0;
+    bool cand = false;
+    if (u < n) {
+        if (core[u]) label[u] = SCAN_CORE;
+        else if (memb[u] != -1) label[u] = SCAN_BORDER;
+        else {
+            b = off[u];
+            e = off[u + 1];
+            cand = e - b <= kHeavy;  // longer rows: the heavy kernel's
+            if (!cand) b = e = 0;
         }
     }
-    if (lane == 0) label[u] = SCAN_OUTLIER;
+    const bool heavy = e - b > kCoop;
+    if (cand && !heavy) {
+        int32_t lo = INT32_MAX, hi = -1;
+        bool hub = false;
+        for (int64_t s = b; s < e && !hub; s += 4) {
+            int32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = s + j < e ? adj[s + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t id = w[j] >= 0 ? memb[w[j]] : -1;
+                if (id == kMulti) hub = true;
+                if (id >= 0) {
+                    lo = min(lo, id);
+                    hi = max(hi, id);
+                }
+            }
+            hub = hub || (hi >= 0 && lo != hi);
+        }
+        label[u] = hub ? SCAN_HUB : SCAN_OUTLIER;
+    }
+    for (unsigned hv = __ballot_sync(0xffffffffu, cand && heavy); hv; hv &= hv - 1) {
+        const int src = __ffs(hv) - 1;
+        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+        int32_t lo = INT32_MAX, hi = -1;
+        bool multi = false, hub = false;
+        for (int64_t s0 = hb; s0 < he && !hub; s0 += 4 * kWarp) {
+            int32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t s = s0 + j * kWarp + lane;
+                w[j] = s < he ? adj[s] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t id = w[j] >= 0 ? memb[w[j]] : -1;
+                multi |= id == kMulti;
+                if (id >= 0) {
+                    lo = min(lo, id);
+                    hi = max(hi, id);
+                }
+            }
+            const int32_t glo = __reduce_min_sync(0xffffffffu, lo);
+            const int32_t ghi = __reduce_max_sync(0xffffffffu, hi);
+            hub = __any_sync(0xffffffffu, multi) || (ghi >= 0 && glo != ghi);
+        }
+        if (lane == src) label[u] = hub ? SCAN_HUB : SCAN_OUTLIER;
+    }
+}
+
+// CTA per heavy vertex in no cluster: hub or outlier over the whole row.
+__global__ void __launch_bounds__(kBlock) k_label_heavy(const int32_t *__restrict__ heavy,
+                                                       const int64_t *__restrict__ off,
+                                                       const int32_t *__restrict__ adj,
+                                                       const uint8_t *__restrict__ core,
+                                                       const int32_t *__restrict__ memb,
+                                                       uint8_t *__restrict__ label) {
+    __shared__ int red[kBlock / 32];
+    const int32_t u = heavy[blockIdx.x];
+    if (core[u] || memb[u] != -1) return;  // labelled by the per-vertex kernel
+    const int64_t b = off[u], e = off[u + 1];
+    int lo = INT32_MAX, hi = -1, multi = 0;
+    for (int64_t s = b + threadIdx.x; s < e; s += kBlock) {
+        const int32_t id = memb[adj[s]];
+        multi |= id == kMulti;
+        if (id >= 0) {
+            lo = min(lo, id);
+            hi = max(hi, id);
+        }
+    }
+    lo = block_reduce(lo, OpMin(), red);
+    hi = block_reduce(hi, OpMax(), red);
+    multi = block_reduce(multi, OpMax(), red);
+    if (threadIdx.x == 0) label[u] = (multi || (hi >= 0 && lo != hi)) ? SCAN_HUB : SCAN_OUTLIER;
+}
+
+__global__ void k_heavy_list(const int64_t *__restrict__ off, int32_t n, int32_t *__restrict__ list,
+                             unsigned long long *count) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || off[v + 1] - off[v] <= kHeavy) return;
+    const unsigned long long k = atomicAdd(count, 1ull);
+    if (list) list[k] = (int32_t)v;
 }
 
 }  // namespace
+
+// The vertices whose rows exceed kHeavy slots (built once per graph).
+static scan_status heavy_list_build(Graph *g) {
+    Ctx *c = g->ctx;
+    g->n_heavy = 0;
+    if (g->n > 0) {
+        DevBuf cnt;
+        SCAN_TRY(dev_alloc(c, cnt, sizeof(unsigned long long)));
+        auto *count = (unsigned long long *)cnt.ptr;
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(h), c->stream);
+        if (e == cudaSuccess) {
+            k_heavy_list<<<grid_for(g->n, kBlock), kBlock, 0, c->stream>>>((const int64_t *)g->off.ptr, g->n, nullptr,
+                                                                           count);
+            c->launches++;
+            e = cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess && h > 0) {
+            scan_status s = dev_alloc(c, g->heavy, 4 * (size_t)h);
+            if (s != SCAN_OK) {
+                dev_free(c, cnt);
+                return s;
+            }
+            e = cudaMemsetAsync(count, 0, sizeof(h), c->stream);
+            if (e == cudaSuccess) {
+                k_heavy_list<<<grid_for(g->n, kBlock), kBlock, 0, c->stream>>>(
+                    (const int64_t *)g->off.ptr, g->n, (int32_t *)g->heavy.ptr, count);
+                c->launches++;
+                e = cudaGetLastError();
+            }
+        }
+        dev_free(c, cnt);
+        if (e != cudaSuccess) return cuda_fail(e, "heavy vertex list");
+        g->n_heavy = (int32_t)h;
+    }
+    g->heavy_ready = true;
+    return SCAN_OK;
+}
 
 static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp,
                                 int32_t *cn) {
@@ -355,12 +635,18 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
         SCAN_CUDA(cudaGetLastError());
         return SCAN_OK;
     }
-    const unsigned gw = grid_for((int64_t)n * kWarp, kBlock);
+    if (!g->heavy_ready) SCAN_TRY(heavy_list_build(g));
+    const int32_t nh = g->n_heavy;
+    const int32_t *heavy = (const int32_t *)g->heavy.ptr;
     const unsigned gt = grid_for(n, kBlock);
     {
         StageTimer t(c, SCAN_STAGE_CORE);
-        k_core<<<gw, kBlock, 0, st>>>(off, sim, n, qp, core);
+        k_core<<<gt, kBlock, 0, st>>>(off, sim, n, qp, core);
         c->launches++;
+        if (nh > 0) {
+            k_core_heavy<<<nh, kBlock, 0, st>>>(heavy, off, sim, qp, core);
+            c->launches++;
+        }
     }
     {
         StageTimer t(c, SCAN_STAGE_CLUSTER);
@@ -377,21 +663,34 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     int32_t *ucnt = (int32_t *)g->ucnt.ptr;
     int64_t *pair_off = (int64_t *)g->pair_off.ptr;
     int32_t *raw = (int32_t *)g->raw.ptr;
+    int32_t *memb = (int32_t *)g->parent.ptr;  // membership codes once union-find is done
     {
         StageTimer t(c, SCAN_STAGE_BORDER);
-        k_border_count<<<gw, kBlock, 0, st>>>(off, adj, sim, core, n, cnt);
+        k_border_count<<<gt, kBlock, 0, st>>>(off, adj, sim, core, cid, memb, n, cnt);
         c->launches++;
+        if (nh > 0) {
+            k_border_count_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, sim, core, cnt);
+            c->launches++;
+        }
         SCAN_TRY(launch_exclusive_scan_i32_to_i64(c, cnt, cnt_off, n, g->scan_tmp));
-        k_border_fill<<<gw, kBlock, 0, st>>>(off, adj, sim, core, cid, n, cnt_off, raw, ucnt);
+        k_border_fill<<<gt, kBlock, 0, st>>>(off, adj, sim, core, memb, n, cnt_off, raw, ucnt);
         c->launches++;
+        if (nh > 0) {
+            k_border_fill_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, sim, core, memb, cnt_off, raw, ucnt);
+            c->launches++;
+        }
         SCAN_TRY(launch_exclusive_scan_i32_to_i64(c, ucnt, pair_off, n, g->scan_tmp));
         k_border_emit<<<gt, kBlock, 0, st>>>(cnt_off, raw, ucnt, pair_off, n, pairs, pairs_cap, npairs);
         c->launches++;
     }
     {
         StageTimer t(c, SCAN_STAGE_LABEL);
-        k_label<<<gw, kBlock, 0, st>>>(off, adj, core, cid, ucnt, cnt_off, raw, n, label);
+        k_label<<<gt, kBlock, 0, st>>>(off, adj, core, memb, n, label);
         c->launches++;
+        if (nh > 0) {
+            k_label_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, core, memb, label);
+            c->launches++;
+        }
     }
     SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;

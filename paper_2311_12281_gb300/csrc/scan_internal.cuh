@@ -33,6 +33,7 @@ enum : uint32_t {
 constexpr int kWarp = 32;
 
 struct Ctx;
+struct Part;  // out-of-core state of a graph kept in host memory (partition.cu)
 
 // Device allocation accounted against the context's budget.
 struct DevBuf {
@@ -67,7 +68,13 @@ struct Graph {
     int32_t fwd_small = 0;
     bool fwd_ready = false;
     bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
+    int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
+    int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
+    DevBuf heavy;           // int32[n_heavy] vertices whose rows are walked by a whole CTA
+    int32_t n_heavy = 0;
+    bool heavy_ready = false;
+    Part *part = nullptr;   // non-null: the CSR stays in host memory and is streamed in blocks
     // per-query scratch
     DevBuf sim;             // uint8[nnz] 1 = eps-similar
     DevBuf core, cid, parent, label;
@@ -86,7 +93,7 @@ struct Graph {
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
                           &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
-                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &sim, &core, &cid, &parent, &label,
+                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &heavy, &sim, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
         for (DevBuf *b : bufs) f(*b);
     }
@@ -185,6 +192,12 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
                          Graph **out);
 void graph_destroy(Graph *g);
 scan_result *result_new(int32_t n, int64_t k, bool pinned);
+// out of core (partition.cu)
+scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, Graph **out,
+                        int64_t block_slots_hint);
+scan_status part_query(Graph *g, const scan_params &p, scan_result **out);
+void part_release(Graph *g);
+int32_t part_block_count(const Graph *g);
 
 #define SCAN_CUDA(call)                                              \
     do {                                                             \

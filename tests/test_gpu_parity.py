@@ -166,6 +166,33 @@ def test_every_strategy_gives_the_oracle_result(ps, ctx, which):
         dg.free()
 
 
+def test_autotune_keeps_results_exact_and_persists(ps, ctx, tmp_path):
+    path = str(tmp_path / "tune.txt")
+    g = gg.chung_lu(30000, 24.0, 2.1, seed=61)
+    cn = oracle.common_counts(g)
+    dg = ctx.load(g)
+    try:
+        strategy, ms = ps.scan_graph_autotune(dg.handle, path)
+        assert strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH)
+        assert ms > 0 and ps.scan_graph_strategy(dg.handle) == strategy
+        assert not dg.has_cache
+        for (p, q, mu) in [(1, 5, 2), (1, 2, 4)]:
+            assert_same(dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE), oracle.scan_from_counts(g, cn, p, q, mu))
+        lines = open(path).read().split("\n")
+        assert len([ln for ln in lines if ln.strip()]) == 1
+        # a graph of the same shape (a relabelled copy: same n, nnz and
+        # largest degree) takes the stored choice without timing
+        g2 = gg.relabel(g, np.random.default_rng(62).permutation(g.n))
+        dg2 = ctx.load(g2)
+        s2, ms2 = ps.scan_graph_autotune(dg2.handle, path)
+        assert s2 == strategy and abs(ms2 - ms) < 1e-5 * max(1.0, ms)
+        assert len([ln for ln in open(path).read().split("\n") if ln.strip()]) == 1
+        assert_same(dg2.query(1, 2, 3), oracle.scan(g2, 1, 2, 3))
+        dg2.free()
+    finally:
+        dg.free()
+
+
 def test_query_entry_points_agree(ps, ctx):
     g = gg.rmat(12, 16, seed=9)
     dg = ctx.load(g)
