@@ -465,22 +465,29 @@ def main():
     edges_per_step = len(queries) * g.m
     value = world * edges_per_step / (ms_per_step / 1e3)
 
-    # roofline of the similarity stage (the dominant kernel)
+    # roofline of the similarity stage (the dominant kernel), three ways:
+    # SURVEY's per-edge algorithmic bytes B(eps) (what a pruned per-edge
+    # intersection must move for these queries), the kernel's own algorithmic
+    # bytes, and the DRAM traffic ncu measured per launch (profiles/traffic.json)
     sim_ms, sim_n = stage_ms["similarity"]
     strategy = ps.scan_graph_strategy(dg.handle)
-    per_edge_pruned = sum(algorithmic_bytes(g, dmin1, dmax1, p, q) for (p, q, mu) in queries)
-    if args.mode == "recompute" and strategy == ps.SCAN_STRATEGY_FORWARD:
-        b_step = forward_bytes(g) * len(queries)
-        bytes_def = "forward triangle count: streamed out-list suffixes + owner lists + planning + counters"
-    elif args.mode == "recompute":
-        b_step = per_edge_pruned
-        bytes_def = "per-edge intersection of the edges the degrees do not decide"
+    if args.mode == "plain":
+        b_step = full_count_bytes(g, dmin1) * len(queries)
+        bytes_def = "per-edge full count without pruning: 4*sum(d_min) + 8*nnz + 8*(n+1) per query"
     else:
-        b_step = full_count_bytes(g, dmin1) * (len(queries) if args.mode == "plain" else 0)
-        bytes_def = "per-edge full count"
-    achieved = (b_step * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
-    # the per-edge intersection's bytes for the same queries, as a problem-level reference
-    problem_rate = (per_edge_pruned * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+        b_step = sum(algorithmic_bytes(g, dmin1, dmax1, p, q) for (p, q, mu) in queries)
+        bytes_def = ("per-edge intersection of the edges the degrees do not decide: "
+                     "4*sum_{live e}(d_min) + 5*nnz + 8*(n+1) per query")
+    if args.mode == "recompute" and strategy == ps.SCAN_STRATEGY_FORWARD:
+        own_step = forward_bytes(g) * len(queries)
+        own_def = ("triangle enumeration: streamed out-list suffixes (4 B/id) + owner lists + "
+                   "planning reads + counters + similarity bytes + offsets")
+    else:
+        own_step, own_def = b_step, bytes_def
+    if args.mode == "cache":
+        b_step = own_step = 0.0
+    achieved = (b_step * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 and b_step else None
+    own_rate = (own_step * args.steps) / (sim_ms / 1e3) / 1e9 if sim_ms > 0 and own_step else None
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -511,8 +518,9 @@ def main():
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "bytes_per_step": b_step, "bytes_def": bytes_def, "launches": sim_n,
                      "avg_ms": sim_ms / max(sim_n, 1), "strategy": strategy,
-                     "per_edge_bytes_rate_gbs": problem_rate,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                     "kernel_own": {"achieved": own_rate, "frac": (own_rate / peak) if own_rate else None,
+                                    "bytes_per_step": own_step, "bytes_def": own_def},
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage_ms.items()},
         "gpu_launches": launches,
         "clocks": clk,

@@ -38,6 +38,10 @@ void reset_forward_schedule(Graph *g) {
     dev_free(c, g->fwd_items[1]);
     dev_free(c, g->fwd_items[2]);
     g->fwd_items_n[0] = g->fwd_items_n[1] = g->fwd_items_n[2] = 0;
+    dev_free(c, g->fwd_ebase);
+    dev_free(c, g->fwd_elen);
+    dev_free(c, g->fwd_efin);
+    g->fwd_entries = false;
     g->fwd_small = 0;
     g->fwd_ready = false;
 }

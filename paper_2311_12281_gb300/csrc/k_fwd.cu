@@ -30,8 +30,13 @@ constexpr int kFwdChunk = 4096;          // max out(b) elements per CTA table
 constexpr int kFwdUnroll = 8;
 constexpr unsigned long long kSlotEmpty = ~0ull;
 
+// A CTA work item: owner v, value chunk of out(v), slot range [sb, se) of
+// v's row; with precomputed entry lists, the item's entries start at e0 (the
+// nlong long ones first, then the short ones).
 struct FItem {
     int32_t v, chunk, sb, se;
+    int64_t e0;
+    int32_t nlong, nent;
 };
 
 __device__ __forceinline__ uint32_t fhash(int32_t x, int logc) { return ((uint32_t)x * 0x9E3779B1u) >> (32 - logc); }
@@ -421,6 +426,323 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_cta(const FItem *__restrict__ ite
     }
 }
 
+// ------------------------------------------------------------ precomputed entries
+// The entries of a work item (one per in-neighbour a of its owner b with a
+// non-empty stretch of out(a) to stream) depend on the graph only, so they
+// are built once, sorted by length -- long ones (>= kLongEntry ids, coarse
+// descending) first, then short ones (exact descending) -- and every count
+// just streams them.
+constexpr int kLongEntry = 32;  // entries this long are streamed by a whole warp
+constexpr int kEntBuckets = 58; // 27 long (by log2 length) + 31 short (by length)
+
+__device__ __forceinline__ int ent_bucket(int32_t len) {
+    if (len >= kLongEntry) return 26 - (31 - __clz(len) - 5);  // log2 5..31 -> 26..0
+    return 27 + (31 - len);                                    // 31..1 -> 27..57
+}
+
+// Chunk bounds of an item, as ids (id-sorted lists) or rank keys.
+struct ItemBounds {
+    int32_t lo, hi;
+    unsigned long long lo_key, hi_key;
+    bool chunked;
+};
+
+__device__ __forceinline__ ItemBounds item_bounds(const FItem &it, const int32_t *__restrict__ deg,
+                                                  const int32_t *__restrict__ fadj, int64_t fb, int32_t ob) {
+    ItemBounds r;
+    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob);
+    r.chunked = ob > kFwdChunk;
+    r.lo = tb == 0 ? INT32_MIN : fadj[fb + tb];
+    r.hi = te == ob ? INT32_MAX : fadj[fb + te];
+    r.lo_key = tb == 0 ? 0ull : rank_key(deg, r.lo);
+    r.hi_key = te == ob ? ~0ull : rank_key(deg, r.hi);
+    return r;
+}
+
+// Entry of row slot s of owner b: stretch [fa + start, fa + start + len) of
+// out(a) and the fcnt index of (a, b); len = 0 when there is none.
+__device__ __forceinline__ int32_t item_entry(int64_t s, int32_t b, int32_t db, const ItemBounds &ib,
+                                              const int32_t *__restrict__ adj, const int32_t *__restrict__ deg,
+                                              const int64_t *__restrict__ foff, const int32_t *__restrict__ fadj,
+                                              const uint32_t *__restrict__ fin, int rank_sorted, int32_t *base,
+                                              uint32_t *fab) {
+    const int32_t a = adj[s], da = deg[a];
+    if (!dev::rank_less(da, a, db, b)) return 0;
+    const int64_t fa = foff[a];
+    const int32_t oa = (int32_t)(foff[a + 1] - fa);
+    const int32_t *row = fadj + fa;
+    int32_t start = 0, end = oa;
+    *fab = fin[s];
+    if (rank_sorted) {
+        // common neighbours of a and b rank above b: the suffix after b
+        start = (int32_t)((int64_t)*fab - fa) + 1;
+        if (ib.chunked) {
+            start = max(start, rank_lower_bound(row, oa, deg, ib.lo_key));
+            end = ib.hi_key == ~0ull ? oa : rank_lower_bound(row, oa, deg, ib.hi_key);
+        }
+    } else if (ib.chunked && oa > 0) {
+        start = ib.lo == INT32_MIN ? 0 : lower_bound_row(row, oa, ib.lo);
+        end = ib.hi == INT32_MAX ? oa : lower_bound_row(row, oa, ib.hi);
+    }
+    *base = (int32_t)(fa + start);  // fadj indices are < m < 2^31
+    return max(end - start, 0);
+}
+
+// CTA per item: number of entries
+__global__ void __launch_bounds__(256) k_fwd_ent_count(const FItem *__restrict__ items, int64_t nitems,
+                                                       const int64_t *__restrict__ off,
+                                                       const int32_t *__restrict__ adj,
+                                                       const int32_t *__restrict__ deg,
+                                                       const int64_t *__restrict__ foff,
+                                                       const int32_t *__restrict__ fadj,
+                                                       const uint32_t *__restrict__ fin, int rank_sorted,
+                                                       int32_t *__restrict__ nent) {
+    __shared__ int32_t wsum[256 / 32 + 1];
+    const FItem it = items[blockIdx.x];
+    const int32_t b = it.v;
+    const int64_t rb = off[b], fb = foff[b];
+    const int32_t db = (int32_t)(off[b + 1] - rb), ob = (int32_t)(foff[b + 1] - fb);
+    const ItemBounds ib = item_bounds(it, deg, fadj, fb, ob);
+    int32_t cnt = 0;
+    for (int32_t rel = it.sb + threadIdx.x; rel < it.se; rel += 256) {
+        int32_t base;
+        uint32_t fab;
+        cnt += item_entry(rb + rel, b, db, ib, adj, deg, foff, fadj, fin, rank_sorted, &base, &fab) > 0;
+    }
+    int32_t total;
+    fblock_scan<256, int32_t>(cnt, &total, wsum);
+    if (threadIdx.x == 0) nent[blockIdx.x] = total;
+}
+
+// CTA per item: the entries, bucketed by length, from eoff[item] on
+__global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items, int64_t nitems,
+                                                       const int64_t *__restrict__ eoff, int64_t ebase_shift,
+                                                       const int64_t *__restrict__ off,
+                                                       const int32_t *__restrict__ adj,
+                                                       const int32_t *__restrict__ deg,
+                                                       const int64_t *__restrict__ foff,
+                                                       const int32_t *__restrict__ fadj,
+                                                       const uint32_t *__restrict__ fin, int rank_sorted,
+                                                       int32_t *__restrict__ e_base, int32_t *__restrict__ e_len,
+                                                       uint32_t *__restrict__ e_fin) {
+    __shared__ int32_t hist[kEntBuckets], boff[kEntBuckets];
+    FItem it = items[blockIdx.x];
+    const int32_t b = it.v;
+    const int64_t rb = off[b], fb = foff[b];
+    const int32_t db = (int32_t)(off[b + 1] - rb), ob = (int32_t)(foff[b + 1] - fb);
+    const ItemBounds ib = item_bounds(it, deg, fadj, fb, ob);
+    for (int k = threadIdx.x; k < kEntBuckets; k += 256) hist[k] = 0;
+    __syncthreads();
+    for (int32_t rel = it.sb + threadIdx.x; rel < it.se; rel += 256) {
+        int32_t base;
+        uint32_t fab;
+        const int32_t len = item_entry(rb + rel, b, db, ib, adj, deg, foff, fadj, fin, rank_sorted, &base, &fab);
+        if (len > 0) atomicAdd(&hist[ent_bucket(len)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0, nlong = 0;
+        for (int k = 0; k < kEntBuckets; ++k) {
+            boff[k] = acc;
+            acc += hist[k];
+            if (k == 26) nlong = acc;
+            hist[k] = 0;
+        }
+        it.e0 = ebase_shift + eoff[blockIdx.x];
+        it.nlong = nlong;
+        it.nent = acc;
+        items[blockIdx.x] = it;
+    }
+    __syncthreads();
+    const int64_t e0 = ebase_shift + eoff[blockIdx.x];
+    for (int32_t rel = it.sb + threadIdx.x; rel < it.se; rel += 256) {
+        int32_t base;
+        uint32_t fab;
+        const int32_t len = item_entry(rb + rel, b, db, ib, adj, deg, foff, fadj, fin, rank_sorted, &base, &fab);
+        if (len > 0) {
+            const int k = ent_bucket(len);
+            const int64_t e = e0 + boff[k] + atomicAdd(&hist[k], 1);
+            e_base[e] = base;
+            e_len[e] = len;
+            e_fin[e] = fab;
+        }
+    }
+}
+
+// Table of the streaming kernel: buckets of four keys (16 bytes, one 128-bit
+// shared-memory load) and a count per key slot. A key that finds its bucket
+// full goes to a small stash; only if the stash is full too does it probe
+// the following buckets. Lookups check the stash and probe further only when
+// the CTA-wide flags say some key went there, so in the common case a lookup
+// is one load and four compares. Empty key: -1.
+constexpr int kStash = 64;
+
+struct FTable {
+    int4 *kb;    // 2^lognb buckets of 4 keys
+    int *cnt;    // 4 * 2^lognb slot counts, then kStash stash counts
+    int *stash;  // kStash stash keys
+    int *meta;   // [0] stash fill, [1] keys that probed past a full stash
+    int lognb;
+};
+
+__device__ __forceinline__ void ft_insert(const FTable &t, int32_t key) {
+    const uint32_t mask = (1u << t.lognb) - 1u;
+    const uint32_t h0 = fhash(key, t.lognb);
+    int *w = (int *)(t.kb + h0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (atomicCAS(w + j, -1, key) == -1) return;
+    const int sp = atomicAdd(t.meta + 0, 1);
+    if (sp < kStash) {
+        t.stash[sp] = key;
+        return;
+    }
+    atomicAdd(t.meta + 1, 1);
+    for (uint32_t it = 1, h = (h0 + 1) & mask; it <= mask; ++it, h = (h + 1) & mask) {
+        int *v = (int *)(t.kb + h);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (atomicCAS(v + j, -1, key) == -1) return;
+    }
+}
+
+// count index of key, or -1; stash_n / spilled are the CTA-wide flags
+__device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key, int stash_n, int spilled) {
+    const uint32_t h0 = fhash(key, t.lognb);
+    const int4 bk = t.kb[h0];
+    int32_t r = -1;
+    r = bk.x == key ? (int32_t)(4 * h0) : r;
+    r = bk.y == key ? (int32_t)(4 * h0 + 1) : r;
+    r = bk.z == key ? (int32_t)(4 * h0 + 2) : r;
+    r = bk.w == key ? (int32_t)(4 * h0 + 3) : r;
+    if (stash_n > 0 && r < 0) {
+        const int ns = min(stash_n, kStash);
+        for (int i = 0; i < ns; ++i)
+            if (t.stash[i] == key) r = (4 << t.lognb) + i;
+    }
+    if (spilled > 0 && r < 0 && bk.w != -1) {
+        const uint32_t mask = (1u << t.lognb) - 1u;
+        for (uint32_t it = 1, h = (h0 + 1) & mask; it <= mask; ++it, h = (h + 1) & mask) {
+            const int4 c = t.kb[h];
+            if (c.x == key) { r = (int32_t)(4 * h); break; }
+            if (c.y == key) { r = (int32_t)(4 * h + 1); break; }
+            if (c.z == key) { r = (int32_t)(4 * h + 2); break; }
+            if (c.w == key) { r = (int32_t)(4 * h + 3); break; }
+            if (c.w == -1) break;
+        }
+    }
+    return r;
+}
+
+constexpr int kEntBlock = 512;
+constexpr int kEntUnroll = 8;
+
+// One CTA per item, streaming its precomputed entries: long entries one per
+// warp (taken in turn, lanes on consecutive ids), then short ones 32 at a
+// time, one per lane (neighbours in the sorted order have about the same
+// length, so the lanes stay busy). A hit c adds one to (b, c) in the table,
+// to (a, c) at the streamed slot in global memory, and -- summed over the
+// entry -- to (a, b). Dynamic shared memory: the table.
+__global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__ items,
+                                                       const int64_t *__restrict__ foff,
+                                                       const int32_t *__restrict__ fadj,
+                                                       const int32_t *__restrict__ e_base,
+                                                       const int32_t *__restrict__ e_len,
+                                                       const uint32_t *__restrict__ e_fin,
+                                                       int32_t *__restrict__ fcnt, int cap_lognb, int load_shift) {
+    extern __shared__ int4 tsm[];
+    __shared__ int32_t next_long, next_short;
+    __shared__ int tmeta[2];
+    const FItem it = items[blockIdx.x];
+    const int32_t b = it.v;
+    const int64_t fb = foff[b];
+    const int32_t ob = (int32_t)(foff[b + 1] - fb);
+    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
+    FTable t;
+    t.lognb = min(cap_lognb, max(3, fceil_log2(tlen << load_shift)));
+    t.kb = tsm;
+    t.cnt = (int *)(tsm + (1 << cap_lognb));
+    t.stash = t.cnt + (4 << cap_lognb) + kStash;
+    t.meta = tmeta;
+    for (int k = threadIdx.x; k < (1 << t.lognb); k += kEntBlock) {
+        t.kb[k] = make_int4(-1, -1, -1, -1);
+        reinterpret_cast<int4 *>(t.cnt)[k] = make_int4(0, 0, 0, 0);
+    }
+    for (int k = threadIdx.x; k < kStash; k += kEntBlock) t.cnt[(4 << t.lognb) + k] = 0;
+    if (threadIdx.x == 0) {
+        tmeta[0] = tmeta[1] = 0;
+        next_long = next_short = 0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < tlen; k += kEntBlock) ft_insert(t, fadj[fb + tb + k]);
+    __syncthreads();
+    const int stash_n = tmeta[0], spilled = tmeta[1];
+    const int lane = threadIdx.x & 31;
+    const int32_t nlong = it.nlong, nshort = it.nent - it.nlong;
+    // long entries: a warp per entry
+    for (int32_t guard = 0; guard <= nlong; ++guard) {
+        int32_t k = 0;
+        if (lane == 0) k = atomicAdd(&next_long, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nlong) break;
+        const int64_t e = it.e0 + k;
+        const int32_t eb = e_base[e], el = e_len[e];
+        int c = 0;
+        for (int32_t j0 = 0; j0 < el; j0 += kWarp * kEntUnroll) {
+            int32_t x[kEntUnroll];
+#pragma unroll
+            for (int u = 0; u < kEntUnroll; ++u) {
+                const int32_t j = j0 + u * kWarp + lane;
+                x[u] = j < el ? __ldg(fadj + eb + j) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kEntUnroll; ++u) {
+                const int32_t r = x[u] >= 0 ? ft_find(t, x[u], stash_n, spilled) : -1;
+                if (r >= 0) {
+                    ++c;
+                    atomicAdd(t.cnt + r, 1);                             // edge (b, c)
+                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);  // edge (a, c)
+                }
+            }
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(fcnt + e_fin[e], c);  // edge (a, b)
+    }
+    // short entries: 32 at a time, one per lane
+    for (int32_t guard = 0; guard <= nshort; guard += kWarp) {
+        int32_t k0 = 0;
+        if (lane == 0) k0 = atomicAdd(&next_short, kWarp);
+        k0 = __shfl_sync(0xffffffffu, k0, 0);
+        if (k0 >= nshort) break;
+        const int32_t k = k0 + lane;
+        if (k < nshort) {
+            const int64_t e = it.e0 + nlong + k;
+            const int32_t eb = e_base[e], el = e_len[e];
+            int c = 0;
+            for (int32_t j0 = 0; j0 < el; j0 += 4) {
+                int32_t x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t r = x[u] >= 0 ? ft_find(t, x[u], stash_n, spilled) : -1;
+                    if (r >= 0) {
+                        ++c;
+                        atomicAdd(t.cnt + r, 1);
+                        atomicAdd(fcnt + (eb + j0 + u), 1);
+                    }
+                }
+            }
+            if (c) atomicAdd(fcnt + e_fin[e], c);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < tlen; k += kEntBlock) {
+        const int32_t r = ft_find(t, fadj[fb + tb + k], stash_n, spilled);
+        if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + fb + tb + k, t.cnt[r]);
+    }
+}
+
 // per forward edge: closed count, mirrored to both slots; optional eps-test
 template <bool WRITE_SIM, bool WRITE_CN>
 __global__ void k_fwd_finish(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ fcnt,
@@ -596,10 +918,84 @@ __global__ void k_fwd_sched_write(const int32_t *__restrict__ deg, const int64_t
     FItem *dst = cls == 1 ? i1 : i2;
     unsigned long long p = atomicAdd(cursor + cls, (unsigned long long)(nchunks * nr));
     for (int32_t c = 0; c < nchunks; ++c)
-        for (int32_t r = 0; r < nr; ++r) dst[p++] = FItem{(int32_t)b, c, r * len, min(db, (r + 1) * len)};
+        for (int32_t r = 0; r < nr; ++r) dst[p++] = FItem{(int32_t)b, c, r * len, min(db, (r + 1) * len), 0, 0, 0};
 }
 
 }  // namespace
+
+// Entry lists of every CTA item (12 bytes per entry, at most one entry per
+// oriented edge and chunk). Without room for them under the budget the
+// counting kernel derives the entries itself, round by round.
+static scan_status fwd_build_entries(Graph *g) {
+    Ctx *c = g->ctx;
+    g->fwd_entries = false;
+    const int64_t n1 = g->fwd_items_n[1], n2 = g->fwd_items_n[2];
+    if (n1 + n2 == 0) return SCAN_OK;
+    const int rs = g->fwd_rank_sorted ? 1 : 0;
+    auto *off = (const int64_t *)g->off.ptr;
+    auto *adj = (const int32_t *)g->adj.ptr;
+    auto *deg = (const int32_t *)g->deg.ptr;
+    auto *foff = (const int64_t *)g->foff.ptr;
+    auto *fadj = (const int32_t *)g->fadj.ptr;
+    auto *fin = (const uint32_t *)g->fin.ptr;
+    DevBuf nent, eoff[3];
+    int64_t total[3] = {0, 0, 0};
+    auto cleanup = [&]() {
+        dev_free(c, nent);
+        dev_free(c, eoff[1]);
+        dev_free(c, eoff[2]);
+    };
+    SCAN_TRY(dev_alloc(c, nent, 4 * (size_t)std::max(n1, n2)));
+    for (int cls = 1; cls <= 2; ++cls) {
+        const int64_t ni = g->fwd_items_n[cls];
+        if (ni == 0) continue;
+        scan_status s = dev_alloc(c, eoff[cls], 8 * ((size_t)ni + 1));
+        if (s != SCAN_OK) {
+            cleanup();
+            return SCAN_OK;  // no room: per-round entries
+        }
+        k_fwd_ent_count<<<(unsigned)ni, 256, 0, c->stream>>>((const FItem *)g->fwd_items[cls].ptr, ni, off, adj, deg,
+                                                            foff, fadj, fin, rs, (int32_t *)nent.ptr);
+        c->launches++;
+        s = launch_exclusive_scan_i32_to_i64(c, (const int32_t *)nent.ptr, (int64_t *)eoff[cls].ptr, ni, g->scan_tmp);
+        if (s != SCAN_OK) {
+            cleanup();
+            return s;
+        }
+        cudaError_t e = cudaMemcpyAsync(&total[cls], (int64_t *)eoff[cls].ptr + ni, 8, cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "forward entry counts");
+        }
+    }
+    const size_t E = (size_t)std::max<int64_t>(total[1] + total[2], 1);
+    if (dev_alloc(c, g->fwd_ebase, 4 * E) != SCAN_OK || dev_alloc(c, g->fwd_elen, 4 * E) != SCAN_OK ||
+        dev_alloc(c, g->fwd_efin, 4 * E) != SCAN_OK) {
+        dev_free(c, g->fwd_ebase);
+        dev_free(c, g->fwd_elen);
+        dev_free(c, g->fwd_efin);
+        cleanup();
+        set_error("");
+        return SCAN_OK;  // no room: per-round entries
+    }
+    for (int cls = 1; cls <= 2; ++cls) {
+        const int64_t ni = g->fwd_items_n[cls];
+        if (ni == 0) continue;
+        k_fwd_ent_write<<<(unsigned)ni, 256, 0, c->stream>>>(
+            (FItem *)g->fwd_items[cls].ptr, ni, (const int64_t *)eoff[cls].ptr, cls == 2 ? total[1] : 0, off, adj,
+            deg, foff, fadj, fin, rs, (int32_t *)g->fwd_ebase.ptr, (int32_t *)g->fwd_elen.ptr,
+            (uint32_t *)g->fwd_efin.ptr);
+        c->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "forward entries");
+    g->fwd_entries = true;
+    return SCAN_OK;
+}
 
 scan_status fwd_prepare(Graph *g) {
     Ctx *c = g->ctx;
@@ -680,6 +1076,7 @@ scan_status fwd_prepare(Graph *g) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, cnts);
     if (e != cudaSuccess) return cuda_fail(e, "forward schedule");
+    SCAN_TRY(fwd_build_entries(g));
     g->fwd_ready = true;
     return SCAN_OK;
 }
@@ -698,8 +1095,24 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     auto *fcnt = (int32_t *)g->fcnt.ptr;
     SCAN_CUDA(cudaMemsetAsync(fcnt, 0, 4 * (size_t)g->m, st));
     const int rs = g->fwd_rank_sorted ? 1 : 0;
+    if (g->fwd_entries) {
+        for (int cls = 2; cls >= 1; --cls) {
+            if (g->fwd_items_n[cls] == 0) continue;
+            // class 1 (out-degree <= 1024): two buckets (eight key slots) per
+            // key, up to 2048 buckets; class 2 (chunks of up to 4096 keys): one
+            // bucket per key, up to 4096; 32 bytes per bucket (keys + counts)
+            // plus the stash: 64.5 KB and 128.5 KB
+            const int cap_lognb = cls == 2 ? 12 : 11, load_shift = cls == 2 ? 0 : 1;
+            const size_t smem = (size_t)(2 * sizeof(int4) << cap_lognb) + 2 * kStash * sizeof(int);
+            SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_fwd_ent<<<(unsigned)g->fwd_items_n[cls], kEntBlock, smem, st>>>(
+                (const FItem *)g->fwd_items[cls].ptr, foff, fadj, (const int32_t *)g->fwd_ebase.ptr,
+                (const int32_t *)g->fwd_elen.ptr, (const uint32_t *)g->fwd_efin.ptr, fcnt, cap_lognb, load_shift);
+            c->launches++;
+        }
+    }
     auto kern = k_fwd_cta<512>;
-    for (int cls = 2; cls >= 1; --cls) {
+    for (int cls = 2; cls >= 1 && !g->fwd_entries; --cls) {
         if (g->fwd_items_n[cls] == 0) continue;
         // class 1 (out-degree <= 1024): 4 buckets per key, up to 4096 (64 KB);
         // class 2 (chunks of up to 4096 keys): 2 buckets per key, up to 8192 (128 KB)

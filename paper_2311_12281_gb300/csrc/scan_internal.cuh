@@ -67,6 +67,8 @@ struct Graph {
     int64_t fwd_items_n[3] = {0, 0, 0};
     int32_t fwd_small = 0;
     bool fwd_ready = false;
+    DevBuf fwd_ebase, fwd_elen, fwd_efin;  // precomputed entries of the CTA items (start in fadj, length, (a, b) index)
+    bool fwd_entries = false;              // entries built (else the kernel derives them per round)
     bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
@@ -93,7 +95,7 @@ struct Graph {
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
                           &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
-                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &heavy, &sim, &core, &cid, &parent, &label,
+                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy, &sim, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
         for (DevBuf *b : bufs) f(*b);
     }
