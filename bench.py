@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel choice (no autotuner)")
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["sweep", "batch", "serving"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batch", "serving", "outofcore"], default="sweep",
                     help="sweep: the R-MAT scale-22 sweep (default, the headline line); batch: 4,096 "
                          "Chung-Lu graphs in one pass; serving: Poisson query streams against the server")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--big-n", type=int, default=16_000_000, help="serving: vertices of the big Chung-Lu graph")
     ap.add_argument("--big-deg", type=float, default=72.0, help="serving: mean sampled degree of the big graph")
     ap.add_argument("--pool", type=int, default=256, help="serving: R-MAT pool graphs (scales 12-18)")
+    ap.add_argument("--ooc-scale", type=int, default=27, help="out of core: R-MAT scale")
+    ap.add_argument("--ooc-budget-gb", type=float, default=8.0, help="out of core: device budget (GB)")
+    ap.add_argument("--no-resident", action="store_true", help="out of core: skip the resident comparison")
     return ap.parse_args()
 
 
@@ -379,6 +382,61 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- out of core
+def run_outofcore(args):
+    """R-MAT scale 27 (edge factor 16, seed 5) kept in pinned host memory and
+    clustered at eps = 1/2, mu = 5 by the partitioned driver under an 8 GB
+    device budget, against the same query on the resident graph (no budget)."""
+    import paper_2311_12281_gb300 as ps
+    from paper_2311_12281_gb300 import _build
+
+    _build.build()
+    t = time.perf_counter()
+    g = gg.rmat(args.ooc_scale, 16, seed=5)
+    gen_s = time.perf_counter() - t
+    p, q, mu = 1, 2, 5
+    budget = int(args.ooc_budget_gb * (1 << 30))
+    ctx = ps.Context(0, budget_bytes=budget)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = time.perf_counter()
+    dg = ctx.load_partitioned(g)
+    load_s = time.perf_counter() - t
+    blocks = dg.blocks
+    t = time.perf_counter()
+    r = dg.query(p, q, mu)
+    query_s = time.perf_counter() - t
+    clk = clocks.stop()
+    dev_peak = ctx.device_bytes
+    dg.free()
+    ctx.close()
+    line = {"metric": METRIC, "value": g.m / query_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": query_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"rmat_s{args.ooc_scale}_ef16_outofcore", "n": g.n, "m": g.m, "eps": "1/2",
+                       "mu": mu, "device_budget_bytes": budget, "blocks": blocks,
+                       "host_csr_bytes": g.offsets.nbytes + g.adj.nbytes, "generation_s": gen_s},
+            "e2e": {"value": g.m / (load_s + query_s), "unit": UNIT, "load_s": load_s, "query_s": query_s,
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": r["core"].nbytes + r["cid"].nbytes +
+                    r["label"].nbytes + r["pairs"].nbytes},
+            "device_bytes_after_query": dev_peak, "clocks": clk}
+    if not args.no_resident:
+        # the same query on the resident graph, element by element
+        ctx2 = ps.Context(0)
+        t = time.perf_counter()
+        h = ctx2.load(g)
+        h.query(p, q, mu, ps.SCAN_Q_RECOMPUTE)  # builds the forward lists and schedule
+        t1 = time.perf_counter()
+        r2 = h.query(p, q, mu, ps.SCAN_Q_RECOMPUTE)
+        t2 = time.perf_counter()
+        same = all(np.array_equal(r[k], r2[k]) for k in ("core", "cid", "label", "pairs"))
+        line["resident"] = {"value": g.m / (t2 - t1), "unit": UNIT, "query_s": t2 - t1, "load_and_first_s": t1 - t,
+                            "identical_to_partitioned": bool(same)}
+        h.free()
+        ctx2.close()
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -388,6 +446,8 @@ def main():
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "outofcore":
+        return run_outofcore(args)
 
     import torch
 

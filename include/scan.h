@@ -172,6 +172,9 @@ typedef struct scan_params {
                                    the lower one streamed; skips edges the degrees decide */
 #define SCAN_STRATEGY_BSEARCH 2 /* per edge: binary search of the smaller row in the larger (checkSim
                                    of Algorithm 2); skips edges the degrees decide */
+#define SCAN_STRATEGY_FORWARD_LEAN 3 /* FORWARD without its precomputed per-item entry lists (12 bytes
+                                        per oriented edge): derived round by round, slower; FORWARD
+                                        falls back to it when the lists do not fit the budget */
 /* Select the similarity kernel family used by SCAN_Q_RECOMPUTE and
  * SCAN_Q_BUILD_CACHE on this graph (SCAN_Q_PLAIN always uses BSEARCH without
  * pruning). SCAN_EINVAL for an unknown value. */

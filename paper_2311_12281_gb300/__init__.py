@@ -242,7 +242,7 @@ def scan_graph_has_cache(g: int) -> bool:
     return bool(lib().scan_graph_has_cache(g))
 
 
-SCAN_STRATEGY_FORWARD, SCAN_STRATEGY_OWNER, SCAN_STRATEGY_BSEARCH = 0, 1, 2
+SCAN_STRATEGY_FORWARD, SCAN_STRATEGY_OWNER, SCAN_STRATEGY_BSEARCH, SCAN_STRATEGY_FORWARD_LEAN = 0, 1, 2, 3
 
 
 def scan_graph_set_strategy(g: int, strategy: int):

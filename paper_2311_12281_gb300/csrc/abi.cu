@@ -358,7 +358,8 @@ int32_t scan_graph_has_cache(const scan_graph *g) { return g && g->cache_valid ?
 scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy) {
     if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
     if (g->part) { set_error("not available for a partitioned graph"); return SCAN_EINVAL; }
-    if (strategy != SCAN_STRATEGY_FORWARD && strategy != SCAN_STRATEGY_OWNER && strategy != SCAN_STRATEGY_BSEARCH) {
+    if (strategy != SCAN_STRATEGY_FORWARD && strategy != SCAN_STRATEGY_OWNER && strategy != SCAN_STRATEGY_BSEARCH &&
+        strategy != SCAN_STRATEGY_FORWARD_LEAN) {
         set_error("unknown strategy " + std::to_string(strategy));
         return SCAN_EINVAL;
     }

@@ -42,6 +42,7 @@ void reset_forward_schedule(Graph *g) {
     dev_free(c, g->fwd_elen);
     dev_free(c, g->fwd_efin);
     g->fwd_entries = false;
+    g->fwd_entries_tried = false;
     g->fwd_small = 0;
     g->fwd_ready = false;
 }

@@ -606,7 +606,9 @@ __device__ __forceinline__ void ft_insert(const FTable &t, int32_t key) {
     }
 }
 
-// count index of key, or -1; stash_n / spilled are the CTA-wide flags
+// count index of key, or -1. GENERAL: some key sits in the stash or past its
+// bucket (stash_n / spilled are the CTA-wide counts); otherwise one load.
+template <bool GENERAL>
 __device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key, int stash_n, int spilled) {
     const uint32_t h0 = fhash(key, t.lognb);
     const int4 bk = t.kb[h0];
@@ -615,6 +617,7 @@ __device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key, int sta
     r = bk.y == key ? (int32_t)(4 * h0 + 1) : r;
     r = bk.z == key ? (int32_t)(4 * h0 + 2) : r;
     r = bk.w == key ? (int32_t)(4 * h0 + 3) : r;
+    if (!GENERAL) return r;
     if (stash_n > 0 && r < 0) {
         const int ns = min(stash_n, kStash);
         for (int i = 0; i < ns; ++i)
@@ -634,55 +637,21 @@ __device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key, int sta
     return r;
 }
 
-constexpr int kEntBlock = 512;
 constexpr int kEntUnroll = 8;
 
-// One CTA per item, streaming its precomputed entries: long entries one per
-// warp (taken in turn, lanes on consecutive ids), then short ones 32 at a
-// time, one per lane (neighbours in the sorted order have about the same
-// length, so the lanes stay busy). A hit c adds one to (b, c) in the table,
-// to (a, c) at the streamed slot in global memory, and -- summed over the
-// entry -- to (a, b). Dynamic shared memory: the table.
-__global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__ items,
-                                                       const int64_t *__restrict__ foff,
-                                                       const int32_t *__restrict__ fadj,
-                                                       const int32_t *__restrict__ e_base,
-                                                       const int32_t *__restrict__ e_len,
-                                                       const uint32_t *__restrict__ e_fin,
-                                                       int32_t *__restrict__ fcnt, int cap_lognb, int load_shift) {
-    extern __shared__ int4 tsm[];
-    __shared__ int32_t next_long, next_short;
-    __shared__ int tmeta[2];
-    const FItem it = items[blockIdx.x];
-    const int32_t b = it.v;
-    const int64_t fb = foff[b];
-    const int32_t ob = (int32_t)(foff[b + 1] - fb);
-    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
-    FTable t;
-    t.lognb = min(cap_lognb, max(3, fceil_log2(tlen << load_shift)));
-    t.kb = tsm;
-    t.cnt = (int *)(tsm + (1 << cap_lognb));
-    t.stash = t.cnt + (4 << cap_lognb) + kStash;
-    t.meta = tmeta;
-    for (int k = threadIdx.x; k < (1 << t.lognb); k += kEntBlock) {
-        t.kb[k] = make_int4(-1, -1, -1, -1);
-        reinterpret_cast<int4 *>(t.cnt)[k] = make_int4(0, 0, 0, 0);
-    }
-    for (int k = threadIdx.x; k < kStash; k += kEntBlock) t.cnt[(4 << t.lognb) + k] = 0;
-    if (threadIdx.x == 0) {
-        tmeta[0] = tmeta[1] = 0;
-        next_long = next_short = 0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += kEntBlock) ft_insert(t, fadj[fb + tb + k]);
-    __syncthreads();
-    const int stash_n = tmeta[0], spilled = tmeta[1];
+// Streams the item's entries: long ones one per warp (taken in turn, lanes on
+// consecutive ids), then short ones 32 at a time, one per lane (neighbours in
+// the sorted order have about the same length, so the lanes stay busy).
+template <bool GENERAL>
+__device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t, int stash_n, int spilled,
+                                           const int32_t *__restrict__ fadj, const int32_t *__restrict__ e_base,
+                                           const int32_t *__restrict__ e_len, const uint32_t *__restrict__ e_fin,
+                                           int32_t *__restrict__ fcnt, int32_t *next_long, int32_t *next_short) {
     const int lane = threadIdx.x & 31;
     const int32_t nlong = it.nlong, nshort = it.nent - it.nlong;
-    // long entries: a warp per entry
     for (int32_t guard = 0; guard <= nlong; ++guard) {
         int32_t k = 0;
-        if (lane == 0) k = atomicAdd(&next_long, 1);
+        if (lane == 0) k = atomicAdd(next_long, 1);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= nlong) break;
         const int64_t e = it.e0 + k;
@@ -697,7 +666,7 @@ __global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__
             }
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
-                const int32_t r = x[u] >= 0 ? ft_find(t, x[u], stash_n, spilled) : -1;
+                const int32_t r = x[u] >= 0 ? ft_find<GENERAL>(t, x[u], stash_n, spilled) : -1;
                 if (r >= 0) {
                     ++c;
                     atomicAdd(t.cnt + r, 1);                             // edge (b, c)
@@ -708,10 +677,9 @@ __global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__
         c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0 && c) atomicAdd(fcnt + e_fin[e], c);  // edge (a, b)
     }
-    // short entries: 32 at a time, one per lane
     for (int32_t guard = 0; guard <= nshort; guard += kWarp) {
         int32_t k0 = 0;
-        if (lane == 0) k0 = atomicAdd(&next_short, kWarp);
+        if (lane == 0) k0 = atomicAdd(next_short, kWarp);
         k0 = __shfl_sync(0xffffffffu, k0, 0);
         if (k0 >= nshort) break;
         const int32_t k = k0 + lane;
@@ -725,7 +693,7 @@ __global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__
                 for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int32_t r = x[u] >= 0 ? ft_find(t, x[u], stash_n, spilled) : -1;
+                    const int32_t r = x[u] >= 0 ? ft_find<GENERAL>(t, x[u], stash_n, spilled) : -1;
                     if (r >= 0) {
                         ++c;
                         atomicAdd(t.cnt + r, 1);
@@ -736,9 +704,52 @@ __global__ void __launch_bounds__(kEntBlock) k_fwd_ent(const FItem *__restrict__
             if (c) atomicAdd(fcnt + e_fin[e], c);
         }
     }
+}
+
+// One CTA per item, streaming its precomputed entries. A hit c adds one to
+// (b, c) in the table, to (a, c) at the streamed slot in global memory, and
+// -- summed over the entry -- to (a, b). Dynamic shared memory: the table.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ items, const int64_t *__restrict__ foff,
+                                                   const int32_t *__restrict__ fadj,
+                                                   const int32_t *__restrict__ e_base,
+                                                   const int32_t *__restrict__ e_len,
+                                                   const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
+                                                   int cap_lognb, int load_shift) {
+    extern __shared__ int4 tsm[];
+    __shared__ int32_t next_long, next_short;
+    __shared__ int tmeta[2];
+    const FItem it = items[blockIdx.x];
+    const int32_t b = it.v;
+    const int64_t fb = foff[b];
+    const int32_t ob = (int32_t)(foff[b + 1] - fb);
+    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
+    FTable t;
+    t.lognb = min(cap_lognb, max(3, fceil_log2(tlen << load_shift)));
+    t.kb = tsm;
+    t.cnt = (int *)(tsm + (1 << cap_lognb));
+    t.stash = t.cnt + (4 << cap_lognb) + kStash;
+    t.meta = tmeta;
+    for (int k = threadIdx.x; k < (1 << t.lognb); k += BLOCK) {
+        t.kb[k] = make_int4(-1, -1, -1, -1);
+        reinterpret_cast<int4 *>(t.cnt)[k] = make_int4(0, 0, 0, 0);
+    }
+    for (int k = threadIdx.x; k < kStash; k += BLOCK) t.cnt[(4 << t.lognb) + k] = 0;
+    if (threadIdx.x == 0) {
+        tmeta[0] = tmeta[1] = 0;
+        next_long = next_short = 0;
+    }
     __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += kEntBlock) {
-        const int32_t r = ft_find(t, fadj[fb + tb + k], stash_n, spilled);
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) ft_insert(t, fadj[fb + tb + k]);
+    __syncthreads();
+    const int stash_n = tmeta[0], spilled = tmeta[1];
+    if (stash_n == 0 && spilled == 0)
+        ent_stream<false>(it, t, 0, 0, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+    else
+        ent_stream<true>(it, t, stash_n, spilled, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+    __syncthreads();
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+        const int32_t r = ft_find<true>(t, fadj[fb + tb + k], stash_n, spilled);
         if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + fb + tb + k, t.cnt[r]);
     }
 }
@@ -865,6 +876,11 @@ __global__ void k_fwd_adj(const uint32_t *__restrict__ oe, int64_t m, const int3
     }
 }
 
+// CTA item classes by the owner's out-degree: 0 up to 256 (256-thread CTAs,
+// 16.5 KB tables), 1 up to 1024 (512 threads, 64.5 KB), 2 above (512
+// threads, tables of 4096-key chunks, 128.5 KB)
+__host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
+
 // warp per vertex: work as a middle vertex and the number of items
 __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restrict__ off,
                                                          const int32_t *__restrict__ adj,
@@ -897,12 +913,13 @@ __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restri
     int64_t nr = (int64_t)((w + item_work - 1) / item_work);
     nr = max((int64_t)1, min(nr, (int64_t)(db + 255) / 256));
     nranges[b] = (int32_t)nr;
-    atomicAdd(counts + (ob <= 1024 ? 1 : 2), (unsigned long long)(nchunks * nr));
+    atomicAdd(counts + 1 + fwd_class(ob), (unsigned long long)(nchunks * nr));
 }
 
 __global__ void k_fwd_sched_write(const int32_t *__restrict__ deg, const int64_t *__restrict__ foff, int32_t n,
                                   const int32_t *__restrict__ nranges, unsigned long long *cursor,
-                                  int32_t *__restrict__ small, FItem *__restrict__ i1, FItem *__restrict__ i2) {
+                                  int32_t *__restrict__ small, FItem *__restrict__ i0, FItem *__restrict__ i1,
+                                  FItem *__restrict__ i2) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const int32_t nr = nranges[b];
@@ -914,14 +931,73 @@ __global__ void k_fwd_sched_write(const int32_t *__restrict__ deg, const int64_t
     const int32_t ob = (int32_t)(foff[b + 1] - foff[b]), db = deg[b];
     const int32_t nchunks = (ob + kFwdChunk - 1) / kFwdChunk;
     const int32_t len = (db + nr - 1) / nr;
-    const int cls = ob <= 1024 ? 1 : 2;
-    FItem *dst = cls == 1 ? i1 : i2;
-    unsigned long long p = atomicAdd(cursor + cls, (unsigned long long)(nchunks * nr));
+    const int cls = fwd_class(ob);
+    FItem *dst = cls == 0 ? i0 : (cls == 1 ? i1 : i2);
+    unsigned long long p = atomicAdd(cursor + 1 + cls, (unsigned long long)(nchunks * nr));
     for (int32_t c = 0; c < nchunks; ++c)
         for (int32_t r = 0; r < nr; ++r) dst[p++] = FItem{(int32_t)b, c, r * len, min(db, (r + 1) * len), 0, 0, 0};
 }
 
 }  // namespace
+
+// Items in descending order of their owner's degree (a counting sort over
+// degrees, capped at kDegBuckets - 1): owners of similar rank run at the same
+// time, and the tails of the out-lists they stream stay in L2.
+constexpr int kDegBuckets = 1 << 16;
+
+__global__ void k_item_deg_hist(const FItem *__restrict__ items, int64_t ni, const int32_t *__restrict__ deg,
+                                int32_t *__restrict__ hist) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ni) return;
+    const int32_t d = min(deg[items[i].v], kDegBuckets - 1);
+    atomicAdd(hist + (kDegBuckets - 1 - d), 1);
+}
+
+__global__ void k_item_scatter(const FItem *__restrict__ items, int64_t ni, const int32_t *__restrict__ deg,
+                               const int64_t *__restrict__ boff, int32_t *__restrict__ cur, FItem *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ni) return;
+    const FItem it = items[i];
+    const int k = kDegBuckets - 1 - min(deg[it.v], kDegBuckets - 1);
+    out[boff[k] + atomicAdd(cur + k, 1)] = it;
+}
+
+static scan_status fwd_order_items(Graph *g) {
+    Ctx *c = g->ctx;
+    const int64_t nmax = std::max(g->fwd_items_n[0], std::max(g->fwd_items_n[1], g->fwd_items_n[2]));
+    if (nmax == 0) return SCAN_OK;
+    DevBuf hist, boff, tmp;
+    auto done = [&](scan_status s) {
+        dev_free(c, hist);
+        dev_free(c, boff);
+        dev_free(c, tmp);
+        return s;
+    };
+    if (dev_alloc(c, hist, 4 * (size_t)kDegBuckets) != SCAN_OK ||
+        dev_alloc(c, boff, 8 * ((size_t)kDegBuckets + 1)) != SCAN_OK ||
+        dev_alloc(c, tmp, sizeof(FItem) * (size_t)nmax) != SCAN_OK) {
+        set_error("");
+        return done(SCAN_OK);  // no room: items stay in schedule order
+    }
+    auto *deg = (const int32_t *)g->deg.ptr;
+    for (int cls = 0; cls < 3; ++cls) {
+        const int64_t ni = g->fwd_items_n[cls];
+        if (ni < 2) continue;
+        auto *items = (FItem *)g->fwd_items[cls].ptr;
+        SCAN_CUDA(cudaMemsetAsync(hist.ptr, 0, hist.bytes, c->stream));
+        k_item_deg_hist<<<grid_for(ni, 256), 256, 0, c->stream>>>(items, ni, deg, (int32_t *)hist.ptr);
+        scan_status s = launch_exclusive_scan_i32_to_i64(c, (const int32_t *)hist.ptr, (int64_t *)boff.ptr,
+                                                         kDegBuckets, g->scan_tmp);
+        if (s != SCAN_OK) return done(s);
+        SCAN_CUDA(cudaMemsetAsync(hist.ptr, 0, hist.bytes, c->stream));
+        k_item_scatter<<<grid_for(ni, 256), 256, 0, c->stream>>>(items, ni, deg, (const int64_t *)boff.ptr,
+                                                                 (int32_t *)hist.ptr, (FItem *)tmp.ptr);
+        SCAN_CUDA(cudaMemcpyAsync(items, tmp.ptr, sizeof(FItem) * (size_t)ni, cudaMemcpyDeviceToDevice, c->stream));
+        c->launches += 2;
+    }
+    SCAN_CUDA(cudaGetLastError());
+    return done(SCAN_OK);
+}
 
 // Entry lists of every CTA item (12 bytes per entry, at most one entry per
 // oriented edge and chunk). Without room for them under the budget the
@@ -929,8 +1005,8 @@ __global__ void k_fwd_sched_write(const int32_t *__restrict__ deg, const int64_t
 static scan_status fwd_build_entries(Graph *g) {
     Ctx *c = g->ctx;
     g->fwd_entries = false;
-    const int64_t n1 = g->fwd_items_n[1], n2 = g->fwd_items_n[2];
-    if (n1 + n2 == 0) return SCAN_OK;
+    const int64_t nmax = std::max(g->fwd_items_n[0], std::max(g->fwd_items_n[1], g->fwd_items_n[2]));
+    if (nmax == 0) return SCAN_OK;
     const int rs = g->fwd_rank_sorted ? 1 : 0;
     auto *off = (const int64_t *)g->off.ptr;
     auto *adj = (const int32_t *)g->adj.ptr;
@@ -942,11 +1018,10 @@ static scan_status fwd_build_entries(Graph *g) {
     int64_t total[3] = {0, 0, 0};
     auto cleanup = [&]() {
         dev_free(c, nent);
-        dev_free(c, eoff[1]);
-        dev_free(c, eoff[2]);
+        for (auto &b : eoff) dev_free(c, b);
     };
-    SCAN_TRY(dev_alloc(c, nent, 4 * (size_t)std::max(n1, n2)));
-    for (int cls = 1; cls <= 2; ++cls) {
+    SCAN_TRY(dev_alloc(c, nent, 4 * (size_t)nmax));
+    for (int cls = 0; cls < 3; ++cls) {
         const int64_t ni = g->fwd_items_n[cls];
         if (ni == 0) continue;
         scan_status s = dev_alloc(c, eoff[cls], 8 * ((size_t)ni + 1));
@@ -970,7 +1045,7 @@ static scan_status fwd_build_entries(Graph *g) {
             return cuda_fail(e, "forward entry counts");
         }
     }
-    const size_t E = (size_t)std::max<int64_t>(total[1] + total[2], 1);
+    const size_t E = (size_t)std::max<int64_t>(total[0] + total[1] + total[2], 1);
     if (dev_alloc(c, g->fwd_ebase, 4 * E) != SCAN_OK || dev_alloc(c, g->fwd_elen, 4 * E) != SCAN_OK ||
         dev_alloc(c, g->fwd_efin, 4 * E) != SCAN_OK) {
         dev_free(c, g->fwd_ebase);
@@ -980,11 +1055,12 @@ static scan_status fwd_build_entries(Graph *g) {
         set_error("");
         return SCAN_OK;  // no room: per-round entries
     }
-    for (int cls = 1; cls <= 2; ++cls) {
+    for (int cls = 0; cls < 3; ++cls) {
         const int64_t ni = g->fwd_items_n[cls];
+        const int64_t first = cls == 0 ? 0 : (cls == 1 ? total[0] : total[0] + total[1]);
         if (ni == 0) continue;
         k_fwd_ent_write<<<(unsigned)ni, 256, 0, c->stream>>>(
-            (FItem *)g->fwd_items[cls].ptr, ni, (const int64_t *)eoff[cls].ptr, cls == 2 ? total[1] : 0, off, adj,
+            (FItem *)g->fwd_items[cls].ptr, ni, (const int64_t *)eoff[cls].ptr, first, off, adj,
             deg, foff, fadj, fin, rs, (int32_t *)g->fwd_ebase.ptr, (int32_t *)g->fwd_elen.ptr,
             (uint32_t *)g->fwd_efin.ptr);
         c->launches++;
@@ -1058,11 +1134,10 @@ scan_status fwd_prepare(Graph *g) {
     SCAN_CUDA(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     SCAN_CUDA(cudaStreamSynchronize(c->stream));
     g->fwd_small = (int32_t)h[0];
-    g->fwd_items_n[1] = (int64_t)h[1];
-    g->fwd_items_n[2] = (int64_t)h[2];
+    for (int cls = 0; cls < 3; ++cls) g->fwd_items_n[cls] = (int64_t)h[1 + cls];
     scan_status s = dev_alloc(c, g->fwd_owners, 4 * (size_t)(h[0] + 1));
-    if (s == SCAN_OK) s = dev_alloc(c, g->fwd_items[1], sizeof(FItem) * (size_t)(h[1] + 1));
-    if (s == SCAN_OK) s = dev_alloc(c, g->fwd_items[2], sizeof(FItem) * (size_t)(h[2] + 1));
+    for (int cls = 0; cls < 3 && s == SCAN_OK; ++cls)
+        s = dev_alloc(c, g->fwd_items[cls], sizeof(FItem) * (size_t)(h[1 + cls] + 1));
     if (s != SCAN_OK) {
         dev_free(c, cnts);
         return s;
@@ -1070,13 +1145,14 @@ scan_status fwd_prepare(Graph *g) {
     SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
     k_fwd_sched_write<<<grid_for(n, 256), 256, 0, c->stream>>>(
         (const int32_t *)g->deg.ptr, (const int64_t *)g->foff.ptr, n, nranges, counts,
-        (int32_t *)g->fwd_owners.ptr, (FItem *)g->fwd_items[1].ptr, (FItem *)g->fwd_items[2].ptr);
+        (int32_t *)g->fwd_owners.ptr, (FItem *)g->fwd_items[0].ptr, (FItem *)g->fwd_items[1].ptr,
+        (FItem *)g->fwd_items[2].ptr);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, cnts);
     if (e != cudaSuccess) return cuda_fail(e, "forward schedule");
-    SCAN_TRY(fwd_build_entries(g));
+    SCAN_TRY(fwd_order_items(g));
     g->fwd_ready = true;
     return SCAN_OK;
 }
@@ -1093,29 +1169,46 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     auto *fadj = (const int32_t *)g->fadj.ptr;
     auto *fin = (const uint32_t *)g->fin.ptr;
     auto *fcnt = (int32_t *)g->fcnt.ptr;
+    // entry lists: built on the first count of the default family (not for
+    // the lean one, and not again after they did not fit the budget)
+    const bool lean = g->strategy == SCAN_STRATEGY_FORWARD_LEAN;
+    if (!lean && !g->fwd_entries && !g->fwd_entries_tried) {
+        g->fwd_entries_tried = true;
+        SCAN_TRY(fwd_build_entries(g));
+    }
+    const bool use_entries = !lean && g->fwd_entries;
     SCAN_CUDA(cudaMemsetAsync(fcnt, 0, 4 * (size_t)g->m, st));
     const int rs = g->fwd_rank_sorted ? 1 : 0;
-    if (g->fwd_entries) {
-        for (int cls = 2; cls >= 1; --cls) {
-            if (g->fwd_items_n[cls] == 0) continue;
-            // class 1 (out-degree <= 1024): two buckets (eight key slots) per
-            // key, up to 2048 buckets; class 2 (chunks of up to 4096 keys): one
-            // bucket per key, up to 4096; 32 bytes per bucket (keys + counts)
-            // plus the stash: 64.5 KB and 128.5 KB
-            const int cap_lognb = cls == 2 ? 12 : 11, load_shift = cls == 2 ? 0 : 1;
+    if (use_entries) {
+        for (int cls = 2; cls >= 0; --cls) {
+            const int64_t ni = g->fwd_items_n[cls];
+            if (ni == 0) continue;
+            // buckets of four keys: two per key (eight slots) in classes 0 and 1,
+            // one per key in class 2; 32 bytes per bucket (keys + counts) plus the stash
+            const int cap_lognb = cls == 0 ? 9 : (cls == 1 ? 11 : 12), load_shift = cls == 2 ? 0 : 1;
             const size_t smem = (size_t)(2 * sizeof(int4) << cap_lognb) + 2 * kStash * sizeof(int);
-            SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_fwd_ent<<<(unsigned)g->fwd_items_n[cls], kEntBlock, smem, st>>>(
-                (const FItem *)g->fwd_items[cls].ptr, foff, fadj, (const int32_t *)g->fwd_ebase.ptr,
-                (const int32_t *)g->fwd_elen.ptr, (const uint32_t *)g->fwd_efin.ptr, fcnt, cap_lognb, load_shift);
+            auto *items = (const FItem *)g->fwd_items[cls].ptr;
+            auto *eb = (const int32_t *)g->fwd_ebase.ptr;
+            auto *el = (const int32_t *)g->fwd_elen.ptr;
+            auto *ef = (const uint32_t *)g->fwd_efin.ptr;
+            if (cls == 0) {
+                SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_lognb,
+                                                                load_shift);
+            } else {
+                SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_lognb,
+                                                                load_shift);
+            }
             c->launches++;
         }
     }
     auto kern = k_fwd_cta<512>;
-    for (int cls = 2; cls >= 1 && !g->fwd_entries; --cls) {
+    for (int cls = 2; cls >= 0 && !use_entries; --cls) {
         if (g->fwd_items_n[cls] == 0) continue;
-        // class 1 (out-degree <= 1024): 4 buckets per key, up to 4096 (64 KB);
-        // class 2 (chunks of up to 4096 keys): 2 buckets per key, up to 8192 (128 KB)
+        // classes 0 and 1 (out-degree <= 1024): 4 buckets per key, up to 4096
+        // (64 KB); class 2 (chunks of up to 4096 keys): 2 buckets per key, up
+        // to 8192 (128 KB); the kernel's table is 2^cap_lognb int4 buckets
         const int cap_lognb = cls == 2 ? 13 : 12, load_shift = cls == 2 ? 1 : 2;
         const size_t smem = sizeof(int4) << cap_lognb;
         SCAN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -44,7 +44,12 @@ struct Part {
 
 namespace {
 
-constexpr int kChunkEdges = 64;
+constexpr int kChunkEdges = 64;     // edges per chunk of a light row
+constexpr int kChunkWork = 4096;    // a row of degree d gets chunks of max(1, kChunkWork / d) edges
+
+__device__ __forceinline__ int32_t chunk_edges(int32_t du) {
+    return max(1, min(kChunkEdges, kChunkWork / max(du, 1)));
+}
 constexpr int kUfLimitP = 1 << 22;
 
 inline __device__ bool sbit(const uint32_t *bits, int64_t s) { return (bits[s >> 5] >> (s & 31)) & 1u; }
@@ -98,19 +103,22 @@ __global__ void k_p_range(const int64_t *__restrict__ offi, const int32_t *__res
     const int32_t b = max(a, l);
     ra[r] = a;
     rb[r] = b;
-    nchunks[r] = (b - a + kChunkEdges - 1) / kChunkEdges;
+    const int32_t ce = chunk_edges(len);
+    nchunks[r] = (b - a + ce - 1) / ce;
 }
 
 struct Chunk {
     int32_t r, a, b;
 };
 
-__global__ void k_p_chunks(const int32_t *__restrict__ ra, const int32_t *__restrict__ rb,
-                           const int64_t *__restrict__ pos, int32_t rows_i, Chunk *__restrict__ chunks) {
+__global__ void k_p_chunks(const int64_t *__restrict__ offi, const int32_t *__restrict__ ra,
+                           const int32_t *__restrict__ rb, const int64_t *__restrict__ pos, int32_t rows_i,
+                           Chunk *__restrict__ chunks) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows_i) return;
     int64_t p = pos[r];
-    for (int32_t a = ra[r]; a < rb[r]; a += kChunkEdges) chunks[p++] = Chunk{(int32_t)r, a, min(rb[r], a + kChunkEdges)};
+    const int32_t ce = chunk_edges((int32_t)(offi[r + 1] - offi[r]));
+    for (int32_t a = ra[r]; a < rb[r]; a += ce) chunks[p++] = Chunk{(int32_t)r, a, min(rb[r], a + ce)};
 }
 
 // warp per chunk: closed common count of each edge, exact eps-test, both
@@ -157,17 +165,24 @@ __global__ void __launch_bounds__(256) k_p_similar(const Chunk *__restrict__ chu
                 }
                 c = __reduce_add_sync(0xffffffffu, c) + 2;
             }
-            if (lane == 0) {
-                // mirror slot: position of u in row v, looked up for every edge
-                // (its absence means an asymmetric input)
-                int32_t lo = 0, hi = dv, pos = -1;
-                for (int it = 0; it < 40 && lo < hi; ++it) {
-                    const int32_t mid = (lo + hi) >> 1;
-                    const int32_t y = rv[mid];
-                    if (y < u) lo = mid + 1;
-                    else if (y > u) hi = mid;
-                    else { pos = mid; break; }
+            // mirror slot: position of u in row v, looked up for every edge (its
+            // absence means an asymmetric input). The warp narrows the range 32
+            // pivots at a time, then checks the last 32 positions at once.
+            int32_t lo = 0, hi = dv;
+            for (int it = 0; it < 8 && hi - lo > kWarp; ++it) {
+                const int32_t step = (hi - lo + kWarp - 1) / kWarp;
+                const int32_t p = lo + lane * step;
+                const unsigned le = __ballot_sync(0xffffffffu, p < hi && rv[p] <= u);
+                if (le == 0) {
+                    hi = lo;  // u below the row's first id
+                    break;
                 }
+                lo += (31 - __clz(le)) * step;
+                hi = min(hi, lo + step);
+            }
+            const unsigned em = __ballot_sync(0xffffffffu, lo + lane < hi && rv[lo + lane] == u);
+            const int32_t pos = em ? lo + __ffs(em) - 1 : -1;
+            if (lane == 0) {
                 if (pos < 0) {
                     atomicOr(err, ERR_LOOP_LIMIT);
                 } else if (!never && (always || dev::eps_similar((uint64_t)c, a1, b1, pp, qq))) {
@@ -494,7 +509,9 @@ scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32
     if (s == SCAN_OK) s = dev_alloc(ctx, g->cnt_off, 8 * R1);   // their offsets
     if (s == SCAN_OK) s = dev_alloc(ctx, g->ucnt, 4 * R1);      // row range starts / unique counts
     if (s == SCAN_OK) s = dev_alloc(ctx, g->pair_off, 8 * R1);  // row range ends (int32 view) / pair offsets
-    if (s == SCAN_OK) s = dev_alloc(ctx, g->src, sizeof(Chunk) * ((size_t)P->max_rows + P->max_slots / kChunkEdges + 2));
+    // chunks: at most one per row plus one per kChunkEdges slots of light rows,
+    // or per slot of the heaviest rows
+    if (s == SCAN_OK) s = dev_alloc(ctx, g->src, sizeof(Chunk) * ((size_t)P->max_rows + P->max_slots + 2));
     if (s == SCAN_OK) s = dev_alloc(ctx, g->npairs, 8);
     if (s != SCAN_OK) return fail(s);
     if (cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -585,9 +602,9 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
                 k_p_range<<<grid_for(rows_i, 256), 256, 0, st>>>(offi, adji, Bi.v0, rows_i, Bi.e0, Bj.v0, Bj.v1, nch,
                                                                 ra, rb);
                 SCAN_TRY(launch_exclusive_scan_i32_to_i64(c, nch, pos, rows_i, g->scan_tmp));
-                k_p_chunks<<<grid_for(rows_i, 256), 256, 0, st>>>(ra, rb, pos, rows_i, (Chunk *)g->src.ptr);
-                // at most rows_i + (slots of block i) / 64 chunks
-                const int64_t bound = (int64_t)rows_i + (Bi.e1 - Bi.e0) / kChunkEdges + 1;
+                k_p_chunks<<<grid_for(rows_i, 256), 256, 0, st>>>(offi, ra, rb, pos, rows_i, (Chunk *)g->src.ptr);
+                // at most one chunk per row plus one per slot of block i
+                const int64_t bound = (int64_t)rows_i + (Bi.e1 - Bi.e0) + 1;
                 k_p_similar<<<grid_for(bound * 32, 256, sim_blocks), 256, 0, st>>>(
                     (const Chunk *)g->src.ptr, pos + rows_i, offi, adji, Bi.v0, Bi.e0,
                     (const int64_t *)P->boff[sj].ptr, (const int32_t *)P->badj[sj].ptr, Bj.v0, Bj.e0, pp, qq, bits,

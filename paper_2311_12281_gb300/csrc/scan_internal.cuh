@@ -69,6 +69,7 @@ struct Graph {
     bool fwd_ready = false;
     DevBuf fwd_ebase, fwd_elen, fwd_efin;  // precomputed entries of the CTA items (start in fadj, length, (a, b) index)
     bool fwd_entries = false;              // entries built (else the kernel derives them per round)
+    bool fwd_entries_tried = false;        // a build was attempted (it is skipped when it does not fit)
     bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item

@@ -151,7 +151,8 @@ def test_every_strategy_gives_the_oracle_result(ps, ctx, which):
     cn = oracle.common_counts(g)
     dg = ctx.load(g)
     try:
-        for strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH):
+        for strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH,
+                         ps.SCAN_STRATEGY_FORWARD_LEAN):
             dg.set_strategy(strategy)
             for (p, q, mu) in [(1, 5, 2), (1, 2, 3), (7, 10, 5)]:
                 assert_same(dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE), oracle.scan_from_counts(g, cn, p, q, mu),
@@ -173,7 +174,8 @@ def test_autotune_keeps_results_exact_and_persists(ps, ctx, tmp_path):
     dg = ctx.load(g)
     try:
         strategy, ms = ps.scan_graph_autotune(dg.handle, path)
-        assert strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH)
+        assert strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH,
+                            ps.SCAN_STRATEGY_FORWARD_LEAN)
         assert ms > 0 and ps.scan_graph_strategy(dg.handle) == strategy
         assert not dg.has_cache
         for (p, q, mu) in [(1, 5, 2), (1, 2, 4)]:
