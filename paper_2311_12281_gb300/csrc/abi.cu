@@ -52,11 +52,14 @@ void dev_free(Ctx *c, DevBuf &b) {
 
 static void graph_release(Graph *g) {
     Ctx *c = g->ctx;
+    query_graph_drop(g);
     g->for_each_buf([c](DevBuf &b) { dev_free(c, b); });
     if (g->h_npairs) cudaFreeHost(g->h_npairs);
     if (g->h_err) cudaFreeHost(g->h_err);
+    if (g->h_qparams) cudaFreeHost(g->h_qparams);
     g->h_npairs = nullptr;
     g->h_err = nullptr;
+    g->h_qparams = nullptr;
 }
 
 scan_status check_params(const scan_params *p) {
@@ -348,6 +351,7 @@ scan_status scan_graph_drop_cache(scan_graph *g) {
     if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
     SCAN_CUDA(cudaSetDevice(g->ctx->device));
     SCAN_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    query_graph_drop(g);
     dev_free(g->ctx, g->cn_cache);
     g->cache_valid = false;
     return SCAN_OK;
@@ -363,6 +367,7 @@ scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy) {
         set_error("unknown strategy " + std::to_string(strategy));
         return SCAN_EINVAL;
     }
+    if (g->strategy != strategy) query_graph_drop(g);
     g->strategy = strategy;
     return SCAN_OK;
 }

@@ -48,6 +48,7 @@ void reset_forward_schedule(Graph *g) {
 }
 
 scan_status apply(Graph *g, const Choice &ch) {
+    query_graph_drop(g);
     g->strategy = ch.strategy;
     if (ch.strategy == SCAN_STRATEGY_FORWARD &&
         (g->fwd_small_work != ch.small_work || g->fwd_item_work != ch.item_work)) {

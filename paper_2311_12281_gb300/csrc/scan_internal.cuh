@@ -74,6 +74,13 @@ struct Graph {
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
+    // one captured query pipeline, replayed as a CUDA graph (query_replay)
+    cudaGraphExec_t qexec = nullptr;
+    uint64_t qkey = 0;
+    uint64_t qlaunches = 0;   // kernels in the captured graph (added to the launch counter per replay)
+    bool qgraph_off = false;  // capture failed once: no more attempts
+    DevBuf qparams;           // uint64[3] parameters the replayed graph reads
+    uint64_t *h_qparams = nullptr;  // pinned staging of the same
     DevBuf heavy;           // int32[n_heavy] vertices whose rows are walked by a whole CTA
     int32_t n_heavy = 0;
     bool heavy_ready = false;
@@ -96,7 +103,8 @@ struct Graph {
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
                           &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
-                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy, &sim, &core, &cid, &parent, &label,
+                          &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
+                          &qparams, &sim, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
         for (DevBuf *b : bufs) f(*b);
     }
@@ -112,17 +120,23 @@ struct QParams {
     const uint64_t *gpp = nullptr;  // [k] per-graph eps_num^2
     const uint64_t *gqq = nullptr;  // [k] per-graph eps_den^2
     const uint32_t *gmu = nullptr;  // [k] per-graph mu
+    const uint64_t *dev = nullptr;  // or one (eps_num^2, eps_den^2, mu) in device memory (graph replays)
     __device__ __forceinline__ void eps(int32_t v, uint64_t &p2, uint64_t &q2) const {
         if (gid) {
             const int32_t g = gid[v];
             p2 = gpp[g];
             q2 = gqq[g];
+        } else if (dev) {
+            p2 = dev[0];
+            q2 = dev[1];
         } else {
             p2 = pp;
             q2 = qq;
         }
     }
-    __device__ __forceinline__ uint32_t mu_of(int32_t v) const { return gid ? gmu[gid[v]] : mu; }
+    __device__ __forceinline__ uint32_t mu_of(int32_t v) const {
+        return gid ? gmu[gid[v]] : (dev ? (uint32_t)dev[2] : mu);
+    }
 };
 
 struct StageMark {
@@ -220,6 +234,13 @@ scan_status launch_exclusive_scan_i32_to_i64(Ctx *c, const int32_t *in, int64_t 
 scan_status graph_prepare(Graph *g);                    // deg, src, rev, validation, oe
 scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *core, int32_t *cid,
                            uint8_t *label, int32_t *pairs, int64_t pairs_cap, int64_t *npairs);
+// The same pipeline for one graph and uniform parameters, replayed as a CUDA
+// graph once it has run once with the same mode and output buffers.
+scan_status query_replay(Graph *g, const scan_params &p, uint32_t mode, uint8_t *core, int32_t *cid, uint8_t *label,
+                         int32_t *pairs, int64_t pairs_cap, int64_t *npairs);
+void query_graph_drop(Graph *g);  // forget the captured graph (buffers or kernel choice changed)
+uint64_t replay_key(uint32_t mode, const void *a, const void *b, const void *c, const void *d, int64_t cap,
+                    const void *e);  // identity of a captured launch sequence
 scan_status build_count_cache(Graph *g);
 scan_status owner_schedule_build(Graph *g);
 scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);

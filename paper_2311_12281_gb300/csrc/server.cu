@@ -60,8 +60,14 @@ struct Done {
     double latency_ms = 0;
 };
 
+// Graphs up to this many slots are served on high-priority streams: their
+// short kernels then take SMs as soon as the long kernels of a big graph's
+// query release them, instead of queueing behind them.
+constexpr int64_t kSmallGraphSlots = int64_t(1) << 24;
+
 struct Slot {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the stream of the request in flight: hi or lo
+    cudaStream_t hi = nullptr, lo = nullptr;
     cudaEvent_t ev = nullptr;
     int state = 0;  // 0 idle, 1 arrays in flight, 2 border pairs in flight
     Request req;
@@ -126,6 +132,7 @@ struct scan_server {
             if (&sg != keep && sg.g && !sg.busy && sg.g->cache_valid && (!best || sg.last_use < best->last_use))
                 best = &sg;
         if (best) {
+            query_graph_drop(best->g);
             dev_free(ctx, best->g->cn_cache);
             best->g->cache_valid = false;
             std::lock_guard<std::mutex> lock(mu);
@@ -200,6 +207,7 @@ struct scan_server {
             return true;
         }
         Graph *g = sg.g;
+        sl.stream = g->nnz <= kSmallGraphSlots ? sl.hi : sl.lo;
         uint32_t mode = SCAN_Q_RECOMPUTE;
         if (opts.use_cache) {
             if (g->cache_valid) {
@@ -225,7 +233,7 @@ struct scan_server {
         }
         {
             StreamScope scope(ctx, sl.stream);
-            s = query_pipeline(g, uniform_params(rq.p), mode, (uint8_t *)g->core.ptr, (int32_t *)g->cid.ptr,
+            s = query_replay(g, rq.p, mode, (uint8_t *)g->core.ptr, (int32_t *)g->cid.ptr,
                                (uint8_t *)g->label.ptr, (int32_t *)g->pairs.ptr, g->nnz, (int64_t *)g->npairs.ptr);
             cudaError_t e = cudaSuccess;
             if (s == SCAN_OK) e = cudaMemcpyAsync(sl.h_np, g->npairs.ptr, 8, cudaMemcpyDeviceToHost, sl.stream);
@@ -370,9 +378,13 @@ scan_status scan_server_create(scan_ctx *ctx, const scan_server_opts *opts, scan
         }
         SCAN_CUDA(cudaSetDevice(ctx->device));
         s->slots.resize((size_t)s->opts.max_inflight);
-        cudaError_t e = cudaStreamCreateWithFlags(&s->load_stream, cudaStreamNonBlocking);
+        int prio_lo = 0, prio_hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->load_stream, cudaStreamNonBlocking);
         for (auto &sl : s->slots) {
-            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.hi, cudaStreamNonBlocking, prio_hi);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.lo, cudaStreamNonBlocking, prio_lo);
+            sl.stream = sl.lo;
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h_np, 8);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h_err, 4);
@@ -530,7 +542,8 @@ void scan_server_destroy(scan_server *s) {
         if (sg.h_adj) cudaFreeHost(sg.h_adj);
     }
     for (auto &sl : s->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream), cudaStreamDestroy(sl.stream);
+        for (cudaStream_t st : {sl.hi, sl.lo})
+            if (st) cudaStreamSynchronize(st), cudaStreamDestroy(st);
         if (sl.ev) cudaEventDestroy(sl.ev);
         void *pin[] = {sl.h_core, sl.h_label, sl.h_cid, sl.h_pairs, sl.h_np, sl.h_err};
         for (void *p : pin)

@@ -89,3 +89,38 @@ def test_batch_rejects_bad_members(ps, ctx):
     with pytest.raises(ps.ScanError):
         ps.scan_batch_query(b, [(0, 1, 2)])
     ps.scan_batch_free(b)
+
+
+def test_replayed_batch_queries_follow_new_parameters(ps, ctx):
+    # the second and later device queries on the same buffers replay a captured
+    # CUDA graph; each must see its own parameters
+    torch = pytest.importorskip("torch")
+    graphs, _ = small_batch(20, seed=4300)
+    b = ps.scan_batch_load(ctx.handle, graphs)
+    try:
+        n = sum(g.n for g in graphs)
+        nnz = sum(g.nnz for g in graphs)
+        core = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        cid = torch.zeros(n, dtype=torch.int32, device="cuda")
+        label = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        pairs = torch.zeros(2 * max(nnz, 1), dtype=torch.int32, device="cuda")
+        npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rng = np.random.default_rng(7)
+        for round_ in range(4):
+            new = [(int(rng.integers(4, 17)), 20, int(rng.integers(2, 9))) for _ in graphs]
+            before = ps.scan_ctx_kernel_launches(ctx.handle)
+            ps.scan_batch_query_device(b, new, ps.SCAN_Q_RECOMPUTE, core.data_ptr(), cid.data_ptr(),
+                                       label.data_ptr(), pairs.data_ptr(), nnz, npairs.data_ptr())
+            ps.scan_ctx_sync(ctx.handle)
+            assert ps.scan_ctx_kernel_launches(ctx.handle) > before  # replays count their kernels too
+            base = 0
+            got_core, got_cid = core.cpu().numpy(), cid.cpu().numpy()
+            for g, (p, q, mu) in zip(graphs, new):
+                want = oracle.scan(g, p, q, mu)
+                assert np.array_equal(got_core[base:base + g.n], want["core"]), f"round {round_}"
+                c = got_cid[base:base + g.n].astype(np.int64)
+                c[c >= 0] -= base
+                assert np.array_equal(c, want["cid"]), f"round {round_}"
+                base += g.n
+    finally:
+        ps.scan_batch_free(b)
