@@ -569,72 +569,38 @@ __global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items
     }
 }
 
-// Table of the streaming kernel: buckets of four keys (16 bytes, one 128-bit
-// shared-memory load) and a count per key slot. A key that finds its bucket
-// full goes to a small stash; only if the stash is full too does it probe
-// the following buckets. Lookups check the stash and probe further only when
-// the CTA-wide flags say some key went there, so in the common case a lookup
-// is one load and four compares. Empty key: -1.
-constexpr int kStash = 64;
-
+// Table of the streaming kernel: open addressing over 32-bit keys (one
+// 32-bit shared-memory load per probe, so a warp's lookups spread over the
+// banks) at a load of at most 1/8 (1/4 for the largest class), linear
+// probing, and a count per slot. Empty key: -1.
 struct FTable {
-    int4 *kb;    // 2^lognb buckets of 4 keys
-    int *cnt;    // 4 * 2^lognb slot counts, then kStash stash counts
-    int *stash;  // kStash stash keys
-    int *meta;   // [0] stash fill, [1] keys that probed past a full stash
-    int lognb;
+    int *keys;  // 2^logs keys
+    int *cnt;   // 2^logs counts
+    int logs;
 };
 
 __device__ __forceinline__ void ft_insert(const FTable &t, int32_t key) {
-    const uint32_t mask = (1u << t.lognb) - 1u;
-    const uint32_t h0 = fhash(key, t.lognb);
-    int *w = (int *)(t.kb + h0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (atomicCAS(w + j, -1, key) == -1) return;
-    const int sp = atomicAdd(t.meta + 0, 1);
-    if (sp < kStash) {
-        t.stash[sp] = key;
-        return;
-    }
-    atomicAdd(t.meta + 1, 1);
-    for (uint32_t it = 1, h = (h0 + 1) & mask; it <= mask; ++it, h = (h + 1) & mask) {
-        int *v = (int *)(t.kb + h);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (atomicCAS(v + j, -1, key) == -1) return;
+    const uint32_t mask = (1u << t.logs) - 1u;
+    uint32_t h = fhash(key, t.logs);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const int old = atomicCAS(t.keys + h, -1, key);
+        if (old == -1 || old == key) return;
+        h = (h + 1) & mask;
     }
 }
 
-// count index of key, or -1. GENERAL: some key sits in the stash or past its
-// bucket (stash_n / spilled are the CTA-wide counts); otherwise one load.
-template <bool GENERAL>
-__device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key, int stash_n, int spilled) {
-    const uint32_t h0 = fhash(key, t.lognb);
-    const int4 bk = t.kb[h0];
-    int32_t r = -1;
-    r = bk.x == key ? (int32_t)(4 * h0) : r;
-    r = bk.y == key ? (int32_t)(4 * h0 + 1) : r;
-    r = bk.z == key ? (int32_t)(4 * h0 + 2) : r;
-    r = bk.w == key ? (int32_t)(4 * h0 + 3) : r;
-    if (!GENERAL) return r;
-    if (stash_n > 0 && r < 0) {
-        const int ns = min(stash_n, kStash);
-        for (int i = 0; i < ns; ++i)
-            if (t.stash[i] == key) r = (4 << t.lognb) + i;
+// slot of key, or -1
+__device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key) {
+    const uint32_t mask = (1u << t.logs) - 1u;
+    uint32_t h = fhash(key, t.logs);
+    int32_t y = t.keys[h];
+    if (y == key) return (int32_t)h;
+    for (uint32_t it = 1; it <= mask && y != -1; ++it) {  // a collision: probe on (rare at this load)
+        h = (h + 1) & mask;
+        y = t.keys[h];
+        if (y == key) return (int32_t)h;
     }
-    if (spilled > 0 && r < 0 && bk.w != -1) {
-        const uint32_t mask = (1u << t.lognb) - 1u;
-        for (uint32_t it = 1, h = (h0 + 1) & mask; it <= mask; ++it, h = (h + 1) & mask) {
-            const int4 c = t.kb[h];
-            if (c.x == key) { r = (int32_t)(4 * h); break; }
-            if (c.y == key) { r = (int32_t)(4 * h + 1); break; }
-            if (c.z == key) { r = (int32_t)(4 * h + 2); break; }
-            if (c.w == key) { r = (int32_t)(4 * h + 3); break; }
-            if (c.w == -1) break;
-        }
-    }
-    return r;
+    return -1;
 }
 
 constexpr int kEntUnroll = 8;
@@ -642,8 +608,7 @@ constexpr int kEntUnroll = 8;
 // Streams the item's entries: long ones one per warp (taken in turn, lanes on
 // consecutive ids), then short ones 32 at a time, one per lane (neighbours in
 // the sorted order have about the same length, so the lanes stay busy).
-template <bool GENERAL>
-__device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t, int stash_n, int spilled,
+__device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
                                            const int32_t *__restrict__ fadj, const int32_t *__restrict__ e_base,
                                            const int32_t *__restrict__ e_len, const uint32_t *__restrict__ e_fin,
                                            int32_t *__restrict__ fcnt, int32_t *next_long, int32_t *next_short) {
@@ -666,7 +631,7 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t, int
             }
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
-                const int32_t r = x[u] >= 0 ? ft_find<GENERAL>(t, x[u], stash_n, spilled) : -1;
+                const int32_t r = x[u] >= 0 ? ft_find(t, x[u]) : -1;
                 if (r >= 0) {
                     ++c;
                     atomicAdd(t.cnt + r, 1);                             // edge (b, c)
@@ -693,7 +658,7 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t, int
                 for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int32_t r = x[u] >= 0 ? ft_find<GENERAL>(t, x[u], stash_n, spilled) : -1;
+                    const int32_t r = x[u] >= 0 ? ft_find(t, x[u]) : -1;
                     if (r >= 0) {
                         ++c;
                         atomicAdd(t.cnt + r, 1);
@@ -708,48 +673,41 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t, int
 
 // One CTA per item, streaming its precomputed entries. A hit c adds one to
 // (b, c) in the table, to (a, c) at the streamed slot in global memory, and
-// -- summed over the entry -- to (a, b). Dynamic shared memory: the table.
+// -- summed over the entry -- to (a, b). Dynamic shared memory: the table
+// (2^cap_logs keys, then 2^cap_logs counts).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ items, const int64_t *__restrict__ foff,
                                                    const int32_t *__restrict__ fadj,
                                                    const int32_t *__restrict__ e_base,
                                                    const int32_t *__restrict__ e_len,
                                                    const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
-                                                   int cap_lognb, int load_shift) {
-    extern __shared__ int4 tsm[];
+                                                   int cap_logs, int load_shift) {
+    extern __shared__ int tsm[];
     __shared__ int32_t next_long, next_short;
-    __shared__ int tmeta[2];
     const FItem it = items[blockIdx.x];
     const int32_t b = it.v;
     const int64_t fb = foff[b];
     const int32_t ob = (int32_t)(foff[b + 1] - fb);
     const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
     FTable t;
-    t.lognb = min(cap_lognb, max(3, fceil_log2(tlen << load_shift)));
-    t.kb = tsm;
-    t.cnt = (int *)(tsm + (1 << cap_lognb));
-    t.stash = t.cnt + (4 << cap_lognb) + kStash;
-    t.meta = tmeta;
-    for (int k = threadIdx.x; k < (1 << t.lognb); k += BLOCK) {
-        t.kb[k] = make_int4(-1, -1, -1, -1);
-        reinterpret_cast<int4 *>(t.cnt)[k] = make_int4(0, 0, 0, 0);
+    t.logs = min(cap_logs, max(5, fceil_log2(tlen << load_shift)));
+    t.keys = tsm;
+    t.cnt = tsm + (1 << cap_logs);
+    for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) {
+        t.keys[k] = -1;
+        t.cnt[k] = 0;
     }
-    for (int k = threadIdx.x; k < kStash; k += BLOCK) t.cnt[(4 << t.lognb) + k] = 0;
     if (threadIdx.x == 0) {
-        tmeta[0] = tmeta[1] = 0;
-        next_long = next_short = 0;
+        next_long = 0;
+        next_short = 0;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < tlen; k += BLOCK) ft_insert(t, fadj[fb + tb + k]);
     __syncthreads();
-    const int stash_n = tmeta[0], spilled = tmeta[1];
-    if (stash_n == 0 && spilled == 0)
-        ent_stream<false>(it, t, 0, 0, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
-    else
-        ent_stream<true>(it, t, stash_n, spilled, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+    ent_stream(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
     __syncthreads();
     for (int k = threadIdx.x; k < tlen; k += BLOCK) {
-        const int32_t r = ft_find<true>(t, fadj[fb + tb + k], stash_n, spilled);
+        const int32_t r = ft_find(t, fadj[fb + tb + k]);
         if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + fb + tb + k, t.cnt[r]);
     }
 }
@@ -1183,21 +1141,23 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
         for (int cls = 2; cls >= 0; --cls) {
             const int64_t ni = g->fwd_items_n[cls];
             if (ni == 0) continue;
-            // buckets of four keys: two per key (eight slots) in classes 0 and 1,
-            // one per key in class 2; 32 bytes per bucket (keys + counts) plus the stash
-            const int cap_lognb = cls == 0 ? 9 : (cls == 1 ? 11 : 12), load_shift = cls == 2 ? 0 : 1;
-            const size_t smem = (size_t)(2 * sizeof(int4) << cap_lognb) + 2 * kStash * sizeof(int);
+            // up to eight slots per key (load 1/8): class 0 always, class 1 up to
+            // 512 keys (4 slots per key above: the 32 KB table lets four
+            // 512-thread CTAs share an SM), class 2 four per key; 8 bytes per
+            // slot (key + count): 16 KB, 32 KB, 128 KB
+            const int cap_logs = cls == 0 ? 11 : (cls == 1 ? 12 : 14), load_shift = cls == 2 ? 2 : 3;
+            const size_t smem = (size_t)(2 * sizeof(int)) << cap_logs;
             auto *items = (const FItem *)g->fwd_items[cls].ptr;
             auto *eb = (const int32_t *)g->fwd_ebase.ptr;
             auto *el = (const int32_t *)g->fwd_elen.ptr;
             auto *ef = (const uint32_t *)g->fwd_efin.ptr;
             if (cls == 0) {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_lognb,
+                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
                                                                 load_shift);
             } else {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_lognb,
+                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
                                                                 load_shift);
             }
             c->launches++;
