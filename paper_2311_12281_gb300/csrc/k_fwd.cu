@@ -603,7 +603,7 @@ __device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key) {
     return -1;
 }
 
-constexpr int kEntUnroll = 8;
+constexpr int kEntUnroll = 4;
 
 // Streams the item's entries: long ones one per warp (taken in turn, lanes on
 // consecutive ids), then short ones 32 at a time, one per lane (neighbours in
@@ -622,7 +622,24 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
         const int64_t e = it.e0 + k;
         const int32_t eb = e_base[e], el = e_len[e];
         int c = 0;
-        for (int32_t j0 = 0; j0 < el; j0 += kWarp * kEntUnroll) {
+        // whole groups of kEntUnroll * 32 ids: every lane busy, no bounds checks
+        int32_t j0 = 0;
+        for (; j0 + kWarp * kEntUnroll <= el; j0 += kWarp * kEntUnroll) {
+            int32_t x[kEntUnroll];
+#pragma unroll
+            for (int u = 0; u < kEntUnroll; ++u) x[u] = __ldg(fadj + eb + j0 + u * kWarp + lane);
+#pragma unroll
+            for (int u = 0; u < kEntUnroll; ++u) {
+                const int32_t r = ft_find(t, x[u]);
+                if (r >= 0) {
+                    ++c;
+                    atomicAdd(t.cnt + r, 1);                             // edge (b, c)
+                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);  // edge (a, c)
+                }
+            }
+        }
+        // the tail (fewer than kEntUnroll * 32 ids): its loads issued together
+        if (j0 < el) {
             int32_t x[kEntUnroll];
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
@@ -631,11 +648,12 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
             }
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
+                if (j0 + u * kWarp >= el) break;  // warp-uniform: no lane has work left
                 const int32_t r = x[u] >= 0 ? ft_find(t, x[u]) : -1;
                 if (r >= 0) {
                     ++c;
-                    atomicAdd(t.cnt + r, 1);                             // edge (b, c)
-                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);  // edge (a, c)
+                    atomicAdd(t.cnt + r, 1);
+                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);
                 }
             }
         }
