@@ -4,6 +4,8 @@
 // a scan_status; the detail goes to a thread-local message.
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -269,6 +271,58 @@ void graph_destroy(Graph *g) {
     delete static_cast<scan_graph *>(g);
 }
 
+// Pinned host blocks for query results, reused from one result to the next:
+// page-locking and unlocking memory costs far more than the copies into it.
+// Blocks are sized in powers of two; up to kPoolCap bytes of free blocks are
+// kept (the rest is released); the pool lives until the process exits.
+namespace {
+std::mutex g_pool_mu;
+std::multimap<size_t, void *> g_pool;
+size_t g_pool_bytes = 0;
+constexpr size_t kPoolCap = size_t(2) << 30;
+
+size_t pool_size(size_t bytes) {
+    size_t s = 4096;
+    while (s < bytes) s <<= 1;
+    return s;
+}
+
+void *pinned_get(size_t bytes, size_t *cap) {
+    const size_t sz = pool_size(bytes);
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        auto it = g_pool.find(sz);
+        if (it != g_pool.end()) {
+            void *p = it->second;
+            g_pool.erase(it);
+            g_pool_bytes -= sz;
+            *cap = sz;
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *cap = sz;
+    return p;
+}
+
+void pinned_put(void *p, size_t cap) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (g_pool_bytes + cap <= kPoolCap) {
+            g_pool.emplace(cap, p);
+            g_pool_bytes += cap;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+}  // namespace
+
 scan_result *result_new(int32_t n, int64_t k, bool pinned) {
     scan_result *r = new scan_result();
     r->n = n;
@@ -276,11 +330,11 @@ scan_result *result_new(int32_t n, int64_t k, bool pinned) {
     r->pinned = pinned;
     const size_t bn = (size_t)n + 1, bk = 8 * (size_t)k + 8;
     if (pinned) {
-        cudaError_t e = cudaMallocHost(&r->core, bn);
-        if (e == cudaSuccess) e = cudaMallocHost(&r->cid, 4 * bn);
-        if (e == cudaSuccess) e = cudaMallocHost(&r->label, bn);
-        if (e == cudaSuccess) e = cudaMallocHost(&r->pairs, bk);
-        if (e != cudaSuccess) {
+        r->core = (uint8_t *)pinned_get(bn, &r->cap[0]);
+        r->cid = (int32_t *)pinned_get(4 * bn, &r->cap[1]);
+        r->label = (uint8_t *)pinned_get(bn, &r->cap[2]);
+        r->pairs = (int32_t *)pinned_get(bk, &r->cap[3]);
+        if (!r->core || !r->cid || !r->label || !r->pairs) {
             scan_result_free(r);
             return nullptr;
         }
@@ -449,10 +503,10 @@ const int32_t *scan_result_border_pairs(const scan_result *r) { return r ? r->pa
 void scan_result_free(scan_result *r) {
     if (!r) return;
     void *bufs[] = {r->core, r->cid, r->label, r->pairs};
-    for (void *b : bufs) {
-        if (!b) continue;
-        if (r->pinned) cudaFreeHost(b);
-        else free(b);
+    for (int i = 0; i < 4; ++i) {
+        if (!bufs[i]) continue;
+        if (r->pinned) pinned_put(bufs[i], r->cap[i]);
+        else free(bufs[i]);
     }
     delete r;
 }

@@ -3,17 +3,22 @@
 //
 // Orient every edge from its lower to its higher (deg, id) endpoint (the
 // degree-oriented edge array of Section 4.1); out(x) is x's list of higher
-// neighbours, ascending by id. For an edge the open common count
-// |nbr(u) cap nbr(v)| is the number of triangles through it, and each
-// triangle a < b < c (in that order) is found exactly once: at its middle
-// vertex b, when the row out(a) of an in-neighbour a is streamed through a
-// shared-memory table of out(b). A hit c then adds one to each of the three
-// edges: (a, b) through a per-in-edge counter, (b, c) through a per-owner
-// counter in shared memory, and (a, c) by an atomic add at the streamed
-// position of c in out(a). In a degree orientation out-degrees stay below
-// sqrt(2m), so the tables are small and sparse (load <= 1/4), and the work is
-// the sum over oriented edges (a, b) of |out(a)| instead of the
-// sum over edges of min(deg) that a per-edge intersection pays.
+// neighbours, ordered by (deg, id) rank when no list exceeds kSortMax (else
+// by id). For an edge the open common count |nbr(u) cap nbr(v)| is the number
+// of triangles through it, and each triangle a < b < c (in that order) is
+// found exactly once: at its middle vertex b, when out(a) of an in-neighbour
+// a -- with rank-ordered lists only its suffix after b -- is streamed through
+// a shared-memory table of out(b). A hit c then adds one to each of the three
+// edges: (a, b) through the entry's sum, (b, c) through a per-owner counter
+// in shared memory, and (a, c) by an atomic add at the streamed position of
+// c in out(a). In a degree orientation out-degrees stay below sqrt(2m), so
+// the tables are small, and the work is the sum over a of d+(a)(d+(a)-1)/2
+// instead of the sum over edges of min(deg) that a per-edge intersection pays.
+//
+// Kernels: k_fwd_small (warp per small owner), k_fwd_ent (CTA per work item,
+// streaming precomputed entry lists; the default), k_fwd_cta (CTA per work
+// item deriving the entries round by round: the lean family and the fallback
+// when the lists do not fit), k_fwd_finish (closed counts, eps-test, mirror).
 //
 // closed count of an edge = triangles through it + 2 (Definition 2.2 with
 // closed neighbourhoods: both endpoints are in both N[.]).

@@ -163,7 +163,7 @@ scan_status graph_prepare(Graph *g) {
         c->launches++;
     }
     SCAN_CUDA(cudaGetLastError());
-    return owner_schedule_build(g);
+    return SCAN_OK;  // the kernel families build their schedules on first use
 }
 
 }  // namespace scan

@@ -568,6 +568,10 @@ static scan_status launch_owner_t(Graph *g, const QParams &qp, int32_t *cn) {
 
 scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn) {
     if (g->m == 0) return SCAN_OK;
+    if (!g->owner_ready) {
+        SCAN_TRY(owner_schedule_build(g));
+        g->owner_ready = true;
+    }
     if (prune) return launch_owner_t<true, true, false>(g, qp, cn);
     if (write_cn && !write_sim) return launch_owner_t<false, false, true>(g, qp, cn);
     return launch_owner_t<false, true, false>(g, qp, cn);

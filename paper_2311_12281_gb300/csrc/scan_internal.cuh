@@ -49,7 +49,8 @@ struct Graph {
     DevBuf off, adj, src, rev, deg, oe;
     DevBuf cn_cache;        // int32[nnz] closed common counts (cached-count serving)
     bool cache_valid = false;
-    // owner schedule of the shared-memory intersection (built at load)
+    // owner schedule of the shared-memory intersection (built on first use)
+    bool owner_ready = false;
     DevBuf owners_small;    // int32[n_small] owners with deg <= 128
     DevBuf items[4];        // work items of classes 1..3
     int64_t n_items[4] = {0, 0, 0, 0};
@@ -193,7 +194,8 @@ struct scan_result {
     int32_t *cid = nullptr;
     uint8_t *label = nullptr;
     int32_t *pairs = nullptr;
-    bool pinned = false;  // arrays from cudaMallocHost (else malloc)
+    bool pinned = false;  // arrays from the pinned block pool (else malloc)
+    size_t cap[4] = {0, 0, 0, 0};  // pinned block sizes of core, cid, label, pairs
 };
 
 namespace scan {
