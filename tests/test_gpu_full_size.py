@@ -78,3 +78,23 @@ def test_plain_path_matches_on_one_query(ps, s22, loaded):
     g, cn = s22
     ctx, dg = loaded
     assert_same(dg.query(1, 2, 5, ps.SCAN_Q_PLAIN), oracle.scan_from_counts(g, cn, 1, 2, 5), "plain path")
+
+
+def test_cached_queries_beyond_l2_match_recompute(ps):
+    # a graph whose similarity array and count cache are larger than L2: the
+    # cached answers must equal the recompute path's (checked against the
+    # oracle above) on every array, and the cached counts the oracle's on
+    # sampled slots
+    g = gg.chung_lu(2_500_000, 64.0, 2.1, seed=9)
+    assert g.nnz > (1 << 27)
+    with ps.Context(0) as ctx:
+        dg = ctx.load(g)
+        first = dg.query(1, 2, 3, ps.SCAN_Q_BUILD_CACHE)
+        assert_same(first, dg.query(1, 2, 3, ps.SCAN_Q_RECOMPUTE))
+        for (p, q, mu) in [(1, 5, 2), (3, 5, 5), (4, 5, 10)]:
+            assert_same(dg.query(p, q, mu, ps.SCAN_Q_AUTO), dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE),
+                        f"eps={p}/{q} mu={mu}")
+        counts = dg.counts()
+    rng = np.random.default_rng(5)
+    slots = np.sort(rng.choice(g.nnz, 20000, replace=False)).astype(np.int64)
+    assert np.array_equal(counts[slots], oracle.counts_for_slots(g, slots))
