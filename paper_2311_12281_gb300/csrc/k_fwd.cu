@@ -574,17 +574,48 @@ __global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items
     }
 }
 
-// Table of the streaming kernel: open addressing over 32-bit keys (one
-// 32-bit shared-memory load per probe, so a warp's lookups spread over the
-// banks) at a load of at most 1/8 (1/4 for the largest class), linear
-// probing, and a count per slot. Empty key: -1.
+// Table of the streaming kernel: 32-bit keys (empty: -1) and a count per
+// slot. Two-choice cuckoo hashing: a key sits at one of its two hashed slots,
+// so a lookup is two independent shared-memory loads and no loop, and the
+// lanes of a warp never wait on one another's collision chains (with linear
+// probing at load 1/8 almost every warp had a lane on a second probe). Keys
+// are placed by eviction chains; a table with a chain longer than
+// kCuckooKicks is rebuilt with linear probing and looked up that way (a
+// CTA-wide choice, so no lane diverges on it).
 struct FTable {
     int *keys;  // 2^logs keys
     int *cnt;   // 2^logs counts
     int logs;
 };
 
-__device__ __forceinline__ void ft_insert(const FTable &t, int32_t key) {
+constexpr int kCuckooKicks = 64;
+
+// second slot: differs from the first in at least the lowest bit
+__device__ __forceinline__ uint32_t fhash_alt(int32_t x, uint32_t h1, int logc) {
+    return h1 ^ ((((uint32_t)x * 0x85EBCA77u) >> (32 - logc)) | 1u);
+}
+
+// true when placed; false when the chain ran out (a key is then missing)
+__device__ __forceinline__ bool ck_insert(const FTable &t, int32_t key) {
+    uint32_t h = fhash(key, t.logs);
+    for (int it = 0; it < kCuckooKicks; ++it) {
+        const int old = atomicExch(t.keys + h, key);
+        if (old == -1) return true;
+        key = old;  // evicted: it moves to its other slot
+        const uint32_t h1 = fhash(key, t.logs);
+        h = h == h1 ? fhash_alt(key, h1, t.logs) : h1;
+    }
+    return false;
+}
+
+// slot of key (>= 0), or -1; a key of -2 finds nothing
+__device__ __forceinline__ int32_t ck_find(const FTable &t, int32_t key) {
+    const uint32_t h1 = fhash(key, t.logs), h2 = fhash_alt(key, h1, t.logs);
+    const int y1 = t.keys[h1], y2 = t.keys[h2];
+    return y1 == key ? (int32_t)h1 : (y2 == key ? (int32_t)h2 : -1);
+}
+
+__device__ __forceinline__ void lp_insert(const FTable &t, int32_t key) {
     const uint32_t mask = (1u << t.logs) - 1u;
     uint32_t h = fhash(key, t.logs);
     for (uint32_t it = 0; it <= mask; ++it) {
@@ -594,13 +625,12 @@ __device__ __forceinline__ void ft_insert(const FTable &t, int32_t key) {
     }
 }
 
-// slot of key, or -1
-__device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key) {
+__device__ __forceinline__ int32_t lp_find(const FTable &t, int32_t key) {
     const uint32_t mask = (1u << t.logs) - 1u;
     uint32_t h = fhash(key, t.logs);
     int32_t y = t.keys[h];
     if (y == key) return (int32_t)h;
-    for (uint32_t it = 1; it <= mask && y != -1; ++it) {  // a collision: probe on (rare at this load)
+    for (uint32_t it = 1; it <= mask && y != -1; ++it) {
         h = (h + 1) & mask;
         y = t.keys[h];
         if (y == key) return (int32_t)h;
@@ -608,11 +638,18 @@ __device__ __forceinline__ int32_t ft_find(const FTable &t, int32_t key) {
     return -1;
 }
 
+template <bool LP>
+__device__ __forceinline__ int32_t tab_find(const FTable &t, int32_t key) {
+    return LP ? lp_find(t, key) : ck_find(t, key);
+}
+
 constexpr int kEntUnroll = 4;
 
 // Streams the item's entries: long ones one per warp (taken in turn, lanes on
 // consecutive ids), then short ones 32 at a time, one per lane (neighbours in
 // the sorted order have about the same length, so the lanes stay busy).
+// Positions past an entry's end read as -2, which no lookup finds.
+template <bool LP>
 __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
                                            const int32_t *__restrict__ fadj, const int32_t *__restrict__ e_base,
                                            const int32_t *__restrict__ e_len, const uint32_t *__restrict__ e_fin,
@@ -635,7 +672,7 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
             for (int u = 0; u < kEntUnroll; ++u) x[u] = __ldg(fadj + eb + j0 + u * kWarp + lane);
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
-                const int32_t r = ft_find(t, x[u]);
+                const int32_t r = tab_find<LP>(t, x[u]);
                 if (r >= 0) {
                     ++c;
                     atomicAdd(t.cnt + r, 1);                             // edge (b, c)
@@ -649,12 +686,12 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
                 const int32_t j = j0 + u * kWarp + lane;
-                x[u] = j < el ? __ldg(fadj + eb + j) : -1;
+                x[u] = j < el ? __ldg(fadj + eb + j) : -2;
             }
 #pragma unroll
             for (int u = 0; u < kEntUnroll; ++u) {
                 if (j0 + u * kWarp >= el) break;  // warp-uniform: no lane has work left
-                const int32_t r = x[u] >= 0 ? ft_find(t, x[u]) : -1;
+                const int32_t r = tab_find<LP>(t, x[u]);
                 if (r >= 0) {
                     ++c;
                     atomicAdd(t.cnt + r, 1);
@@ -678,10 +715,10 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
             for (int32_t j0 = 0; j0 < el; j0 += 4) {
                 int32_t x[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -1;
+                for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -2;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int32_t r = x[u] >= 0 ? ft_find(t, x[u]) : -1;
+                    const int32_t r = tab_find<LP>(t, x[u]);
                     if (r >= 0) {
                         ++c;
                         atomicAdd(t.cnt + r, 1);
@@ -691,6 +728,16 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
             }
             if (c) atomicAdd(fcnt + e_fin[e], c);
         }
+    }
+}
+
+// the owner's counts, added to its out-edges (b, c)
+template <bool LP, int BLOCK>
+__device__ __forceinline__ void ent_flush(const FTable &t, const int32_t *__restrict__ fadj, int64_t base,
+                                          int32_t tlen, int32_t *__restrict__ fcnt) {
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+        const int32_t r = tab_find<LP>(t, fadj[base + k]);
+        if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + base + k, t.cnt[r]);
     }
 }
 
@@ -706,7 +753,7 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
                                                    const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
                                                    int cap_logs, int load_shift) {
     extern __shared__ int tsm[];
-    __shared__ int32_t next_long, next_short;
+    __shared__ int32_t next_long, next_short, failed;
     const FItem it = items[blockIdx.x];
     const int32_t b = it.v;
     const int64_t fb = foff[b];
@@ -723,15 +770,24 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
     if (threadIdx.x == 0) {
         next_long = 0;
         next_short = 0;
+        failed = 0;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) ft_insert(t, fadj[fb + tb + k]);
+    for (int k = threadIdx.x; k < tlen; k += BLOCK)
+        if (!ck_insert(t, fadj[fb + tb + k])) failed = 1;
     __syncthreads();
-    ent_stream(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
-    __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
-        const int32_t r = ft_find(t, fadj[fb + tb + k]);
-        if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + fb + tb + k, t.cnt[r]);
+    if (failed) {  // an eviction chain ran out: linear probing for this table
+        for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) t.keys[k] = -1;
+        __syncthreads();
+        for (int k = threadIdx.x; k < tlen; k += BLOCK) lp_insert(t, fadj[fb + tb + k]);
+        __syncthreads();
+        ent_stream<true>(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+        __syncthreads();
+        ent_flush<true, BLOCK>(t, fadj, fb + tb, tlen, fcnt);
+    } else {
+        ent_stream<false>(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+        __syncthreads();
+        ent_flush<false, BLOCK>(t, fadj, fb + tb, tlen, fcnt);
     }
 }
 
