@@ -238,7 +238,8 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
     const size_t N1 = (size_t)n + 1, E = (size_t)(nnz > 0 ? nnz : 1), M = (size_t)(g->m > 0 ? g->m : 1);
     struct { DevBuf *b; size_t bytes; } plan[] = {
         {&g->off, 8 * N1}, {&g->adj, 4 * E}, {&g->src, 4 * E}, {&g->rev, 4 * E}, {&g->deg, 4 * N1},
-        {&g->oe, 4 * M}, {&g->sim, E}, {&g->core, N1}, {&g->cid, 4 * N1}, {&g->parent, 4 * N1},
+        {&g->oe, 4 * M}, {&g->sim, E}, {&g->simo, (M + 15) & ~(size_t)15}, {&g->nsim, 4 * N1}, {&g->hst, 4 * N1},
+        {&g->mslots, 8}, {&g->core, N1}, {&g->cid, 4 * N1}, {&g->parent, 4 * N1},
         {&g->label, N1}, {&g->cnt, 4 * N1}, {&g->cnt_off, 8 * N1}, {&g->ucnt, 4 * N1}, {&g->pair_off, 8 * N1},
         {&g->raw, 4 * E}, {&g->pairs, 8 * E}, {&g->npairs, 8}, {&g->err, 4}};
     for (auto &p : plan) {
@@ -253,6 +254,8 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
               : cudaMemsetAsync(g->off.ptr, 0, 8, ctx->stream);
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(g->adj.ptr, adj, 4 * (size_t)nnz, kind, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->err.ptr, 0, 4, ctx->stream);
+    // the flags are read 16 at a time: the padding after the last edge stays zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->simo.ptr, 0, g->simo.bytes, ctx->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "graph upload"));
     scan_status s = graph_prepare(g);
     if (s != SCAN_OK) return fail(s);
@@ -406,8 +409,7 @@ scan_status scan_graph_drop_cache(scan_graph *g) {
     SCAN_CUDA(cudaSetDevice(g->ctx->device));
     SCAN_CUDA(cudaStreamSynchronize(g->ctx->stream));
     query_graph_drop(g);
-    dev_free(g->ctx, g->cn_cache);
-    g->cache_valid = false;
+    cache_free(g);
     return SCAN_OK;
 }
 
@@ -432,9 +434,12 @@ scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out) {
     if (!g || !out) { set_error("graph or out is NULL"); return SCAN_EINVAL; }
     if (g->part || !g->cache_valid) { set_error("graph has no common-count cache"); return SCAN_EINVAL; }
     SCAN_CUDA(cudaSetDevice(g->ctx->device));
-    if (g->nnz > 0)
-        SCAN_CUDA(cudaMemcpyAsync(out, g->cn_cache.ptr, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost,
+    if (g->nnz > 0) {
+        // the cache is kept per oriented edge; the border scratch receives it per slot
+        SCAN_TRY(cache_to_slots(g, (int32_t *)g->raw.ptr));
+        SCAN_CUDA(cudaMemcpyAsync(out, g->raw.ptr, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost,
                                   g->ctx->stream));
+    }
     SCAN_CUDA(cudaStreamSynchronize(g->ctx->stream));
     return SCAN_OK;
 }

@@ -173,10 +173,7 @@ extern "C" scan_status scan_graph_autotune(scan_graph *g, const char *cache_path
                 if (best.ms < 0 || t < best.ms) best = ch;
             }
             SCAN_TRY(apply(g, best));
-            if (!had_cache) {
-                dev_free(c, g->cn_cache);
-                g->cache_valid = false;
-            }
+            if (!had_cache) cache_free(g);
             store_choice(cache_path, key, best);
         }
         if (strategy_out) *strategy_out = best.strategy;

@@ -791,24 +791,30 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
     }
 }
 
-// per forward edge: closed count, mirrored to both slots; optional eps-test
+// per forward edge: closed count and either the count cache (count and
+// closed-degree product) or the eps-test (a flag per oriented edge and the
+// endpoints' eps-degrees)
 template <bool WRITE_SIM, bool WRITE_CN>
 __global__ void k_fwd_finish(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ fcnt,
                              const int32_t *__restrict__ src, const int32_t *__restrict__ adj,
-                             const uint32_t *__restrict__ rev, const int32_t *__restrict__ deg, QParams qp,
-                             uint8_t *__restrict__ sim, int32_t *__restrict__ cn) {
+                             const int32_t *__restrict__ deg, QParams qp, uint8_t *__restrict__ simo,
+                             int32_t *__restrict__ nsim, int32_t *__restrict__ cn, uint64_t *__restrict__ dd) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = oe[i];
-        const uint32_t r = rev[e];
         const int32_t c = fcnt[i] + 2;
-        if (WRITE_CN) { cn[e] = c; cn[r] = c; }
+        const int32_t u = src[e], v = adj[e];
+        if (WRITE_CN) {
+            cn[i] = c;
+            dd[i] = ((uint64_t)deg[u] + 1) * ((uint64_t)deg[v] + 1);
+        }
         if (WRITE_SIM) {
-            const int32_t u = src[e], v = adj[e];
             uint64_t pp, qq;
             qp.eps(u, pp, qq);
-            if (dev::eps_similar((uint64_t)c, (uint64_t)deg[u] + 1, (uint64_t)deg[v] + 1, pp, qq)) {
-                sim[e] = 1;
-                sim[r] = 1;
+            const bool s = dev::eps_similar((uint64_t)c, (uint64_t)deg[u] + 1, (uint64_t)deg[v] + 1, pp, qq);
+            simo[i] = s ? 1 : 0;
+            if (s) {
+                atomicAdd(nsim + u, 1);
+                atomicAdd(nsim + v, 1);
             }
         }
     }
@@ -1194,7 +1200,8 @@ scan_status fwd_prepare(Graph *g) {
     return SCAN_OK;
 }
 
-scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn) {
+scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn,
+                              uint64_t *dd) {
     Ctx *c = g->ctx;
     if (g->m == 0) return SCAN_OK;
     SCAN_TRY(fwd_prepare(g));
@@ -1263,14 +1270,14 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     const unsigned gf = grid_for(g->m, 256, c->num_sms * 32);
     auto *oe = (const uint32_t *)g->oe.ptr;
     auto *src = (const int32_t *)g->src.ptr;
-    auto *rev = (const uint32_t *)g->rev.ptr;
-    auto *sim = (uint8_t *)g->sim.ptr;
+    auto *simo = (uint8_t *)g->simo.ptr;
+    auto *nsim = (int32_t *)g->nsim.ptr;
     if (write_sim && write_cn)
-        k_fwd_finish<true, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, rev, deg, qp, sim, cn);
+        k_fwd_finish<true, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
     else if (write_cn)
-        k_fwd_finish<false, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, rev, deg, qp, sim, cn);
+        k_fwd_finish<false, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
     else
-        k_fwd_finish<true, false><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, rev, deg, qp, sim, cn);
+        k_fwd_finish<true, false><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
     c->launches++;
     SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;

@@ -1,15 +1,18 @@
 // k_query.cu -- one SCAN query on a resident graph.
 //
 // Steps (GPUSCAN++ Algorithm 1's three phases, restated):
-//   similarity  per degree-oriented edge: closed common count, exact eps-test,
-//               result mirrored to both slots (Algorithm 2 / checkSim);
-//   cores       |N_eps[u]| = 1 + #similar slots of row u, early exit at mu;
+//   similarity  per degree-oriented edge: closed common count and the exact
+//               eps-test (Algorithm 2 / checkSim), giving a flag per oriented
+//               edge and the eps-degree of every vertex;
+//   cores       |N_eps[u]| = 1 + eps-degree >= mu;
 //   clusters    lock-free union-find over core-core similar edges, hooking
 //               the larger root under the smaller one, so each root is the
 //               smallest core id of its cluster (Algorithm 3 replaced);
 //   borders     every (non-core v, cluster of an eps-similar core) pair,
-//               sorted and unique per vertex;
-//   labels      core / border / hub / outlier (Algorithm 4, by definition).
+//               gathered from the similar edges, sorted and unique per vertex;
+//   labels      core / border / hub / outlier (Algorithm 4, by definition),
+//               the hub test pulled by the vertices in no cluster or pushed
+//               by those in one, whichever walks fewer row slots.
 #include "scan_internal.cuh"
 
 namespace scan {
@@ -71,24 +74,85 @@ __global__ void __launch_bounds__(kBlock) k_isect_bsearch(
     }
 }
 
-// eps-test from cached closed common counts, one thread per oriented edge
+// ------------------------------------------------------------------ similarity outputs
+// Every similarity family ends in the same two arrays: one flag per
+// degree-oriented edge (simo[i] = 1 when the edge oe[i] is eps-similar) and
+// the open eps-degree of every vertex (nsim[u], u itself not counted). The
+// later stages read only these: the cores from nsim, union-find and the
+// border candidates from the similar edges, so a query with few similar
+// edges touches few edges after the similarity stage.
+
+// eps-test from the count cache, one thread per oriented edge: the count and
+// the closed-degree product are read in edge order; vertex data only for the
+// similar edges (and for the graph index of a batch's per-graph parameters)
 __global__ void __launch_bounds__(kBlock) k_sim_from_counts(
-    const int32_t *__restrict__ adj, const int32_t *__restrict__ src, const uint32_t *__restrict__ rev,
-    const int32_t *__restrict__ deg, const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ cn,
-    QParams qp, uint8_t *__restrict__ sim) {
+    const int32_t *__restrict__ adj, const int32_t *__restrict__ src, const uint32_t *__restrict__ oe, int64_t m,
+    const int32_t *__restrict__ cn, const uint64_t *__restrict__ dd, QParams qp, uint8_t *__restrict__ simo,
+    int32_t *__restrict__ nsim) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
+        uint64_t pp, qq;
+        qp.eps(qp.gid ? src[oe[i]] : 0, pp, qq);
+        const bool s = dev::eps_similar_dd((uint64_t)cn[i], dd[i], pp, qq);
+        simo[i] = s ? 1 : 0;
+        if (s) {
+            const uint32_t e = oe[i];
+            atomicAdd(nsim + src[e], 1);
+            atomicAdd(nsim + adj[e], 1);
+        }
+    }
+}
+
+// the count cache from per-slot counts (the per-edge families' output)
+__global__ void __launch_bounds__(kBlock) k_cache_orient(const int32_t *__restrict__ adj,
+                                                        const int32_t *__restrict__ src,
+                                                        const int32_t *__restrict__ deg,
+                                                        const uint32_t *__restrict__ oe, int64_t m,
+                                                        const int32_t *__restrict__ slot_cn, int32_t *__restrict__ cn,
+                                                        uint64_t *__restrict__ dd) {
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
         const uint32_t e = oe[i];
-        const int32_t u = src[e], v = adj[e];
-        uint64_t pp, qq;
-        qp.eps(u, pp, qq);
-        if (dev::eps_similar((uint64_t)cn[e], (uint64_t)deg[u] + 1, (uint64_t)deg[v] + 1, pp, qq)) {
-            sim[e] = 1;
-            sim[rev[e]] = 1;
+        cn[i] = slot_cn[e];
+        dd[i] = ((uint64_t)deg[src[e]] + 1) * ((uint64_t)deg[adj[e]] + 1);
+    }
+}
+
+// and back: both slots of every oriented edge
+__global__ void __launch_bounds__(kBlock) k_cache_slots(const uint32_t *__restrict__ oe,
+                                                       const uint32_t *__restrict__ rev, int64_t m,
+                                                       const int32_t *__restrict__ cn,
+                                                       int32_t *__restrict__ slot_cn) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
+        const uint32_t e = oe[i];
+        slot_cn[e] = cn[i];
+        slot_cn[rev[e]] = cn[i];
+    }
+}
+
+// the per-slot flags of the per-edge families, read once per oriented edge
+__global__ void __launch_bounds__(kBlock) k_sim_orient(const int32_t *__restrict__ adj,
+                                                      const int32_t *__restrict__ src,
+                                                      const uint32_t *__restrict__ oe, int64_t m,
+                                                      const uint8_t *__restrict__ sim, uint8_t *__restrict__ simo,
+                                                      int32_t *__restrict__ nsim) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
+        const uint32_t e = oe[i];
+        const uint8_t s = sim[e];
+        simo[i] = s;
+        if (s) {
+            atomicAdd(nsim + src[e], 1);
+            atomicAdd(nsim + adj[e], 1);
         }
     }
 }
 
 // ------------------------------------------------------------------ cores
+// |N_eps[u]| = 1 + nsim[u] (u is eps-similar to itself)
+__global__ void k_core(const int32_t *__restrict__ nsim, int32_t n, QParams qp, uint8_t *__restrict__ core) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) core[u] = (uint32_t)nsim[u] + 1u >= qp.mu_of((int32_t)u) ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ heavy rows
 // Rows of at most kCoop slots are walked by one thread; longer rows by the
 // whole warp (each warp gathers its threads' long rows and takes them in
 // turn). Most vertices of a power-law graph have short rows, so a warp keeps
@@ -99,51 +163,6 @@ constexpr int kCoop = 32;
 // whole CTA each (the *_heavy kernels below); the per-vertex kernels skip them.
 constexpr int kHeavy = 1024;
 
-// |N_eps[u]| = 1 + similar slots of row u; counting stops once it reaches mu.
-__global__ void __launch_bounds__(kBlock) k_core(const int64_t *__restrict__ off, const uint8_t *__restrict__ sim,
-                                                 int32_t n, QParams qp, uint8_t *__restrict__ core) {
-    const int64_t u = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    int64_t b = 0, e = 0;
-    uint32_t mu = 0;
-    bool mine = false;  // rows above kHeavy are the heavy kernel's
-    if (u < n) {
-        b = off[u];
-        e = off[u + 1];
-        mu = qp.mu_of((int32_t)u);
-        mine = e - b <= kHeavy;
-    }
-    const bool heavy = mine && e - b > kCoop;
-    if (mine && !heavy) {
-        uint32_t cnt = 1;  // u itself: sigma(u, u) = 1
-        for (int64_t s = b; s < e && cnt < mu; s += 4) {
-            uint32_t x = sim[s];
-            if (s + 1 < e) x += sim[s + 1];
-            if (s + 2 < e) x += sim[s + 2];
-            if (s + 3 < e) x += sim[s + 3];
-            cnt += x;
-        }
-        core[u] = cnt >= mu ? 1 : 0;
-    }
-    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
-        const int src = __ffs(hv) - 1;
-        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-        const uint32_t hmu = __shfl_sync(0xffffffffu, mu, src);
-        uint32_t cnt = 1;
-        for (int64_t s0 = hb; s0 < he && cnt < hmu; s0 += 4 * kWarp) {
-            uint32_t x = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t s = s0 + j * kWarp + lane;
-                x += (s < he && sim[s]) ? 1u : 0u;
-            }
-            cnt += __reduce_add_sync(0xffffffffu, x);
-        }
-        if (lane == src) core[u] = cnt >= hmu ? 1 : 0;
-    }
-}
-
-// ------------------------------------------------------------------ heavy rows
 // Block-wide sum / min / max / or of one int per thread (all threads call).
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T x, Op op, T *red) {
@@ -157,21 +176,25 @@ __device__ __forceinline__ T block_reduce(T x, Op op, T *red) {
     return y;
 }
 
-struct OpAdd { __device__ int operator()(int a, int b) const { return a + b; } };
+struct OpAdd { __device__ long long operator()(long long a, long long b) const { return a + b; } };
 struct OpMin { __device__ int operator()(int a, int b) const { return min(a, b); } };
 struct OpMax { __device__ int operator()(int a, int b) const { return max(a, b); } };
 
-// CTA per heavy vertex: |N_eps[u]| over the whole row.
-__global__ void __launch_bounds__(kBlock) k_core_heavy(const int32_t *__restrict__ heavy, const int64_t *__restrict__ off,
-                                                       const uint8_t *__restrict__ sim, QParams qp,
-                                                       uint8_t *__restrict__ core) {
-    __shared__ int red[kBlock / 32];
-    const int32_t u = heavy[blockIdx.x];
-    const int64_t b = off[u], e = off[u + 1];
-    int c = 0;
-    for (int64_t s = b + threadIdx.x; s < e; s += kBlock) c += sim[s];
-    c = block_reduce(c, OpAdd(), red);
-    if (threadIdx.x == 0) core[u] = (uint32_t)c + 1u >= qp.mu_of(u) ? 1 : 0;
+// ------------------------------------------------------------------ similar edges
+// Calls f(i) for every similar oriented edge i, reading the flags 16 at a
+// time (the flag array is padded with zeros to a multiple of 16), so a query
+// with few similar edges streams the flags at full width and skips the rest.
+template <class F>
+__device__ __forceinline__ void for_each_similar(const uint8_t *__restrict__ simo, int64_t m, F f) {
+    const int64_t chunks = (m + 15) >> 4;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < chunks;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 w = reinterpret_cast<const uint4 *>(simo)[k];
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            for (uint32_t x = words[q]; x; x &= x - 1) f(k * 16 + q * 4 + ((__ffs(x) - 1) >> 3));
+    }
 }
 
 // ------------------------------------------------------------------ union-find
@@ -205,17 +228,17 @@ __global__ void k_uf_init(const uint8_t *__restrict__ core, int32_t n, int32_t *
     if (u < n) parent[u] = core[u] ? (int32_t)u : -1;
 }
 
-// one thread per oriented edge: core-core similar edges join clusters
+// core-core similar edges join clusters
 __global__ void __launch_bounds__(kBlock) k_uf_hook(const int32_t *__restrict__ adj, const int32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ oe, int64_t m,
-                                                   const uint8_t *__restrict__ sim, const uint8_t *__restrict__ core,
-                                                   int32_t *parent, uint32_t *err) {
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
+                                                   const uint8_t *__restrict__ simo,
+                                                   const uint8_t *__restrict__ core, int32_t *parent,
+                                                   uint32_t *err) {
+    for_each_similar(simo, m, [&](int64_t i) {
         const uint32_t e = oe[i];
-        if (!sim[e]) continue;
         const int32_t u = src[e], v = adj[e];
         if (core[u] && core[v]) uf_unite(parent, u, v, err);
-    }
+    });
 }
 
 __global__ void k_uf_final(const uint8_t *__restrict__ core, int32_t n, int32_t *parent, int32_t *__restrict__ cid,
@@ -231,63 +254,41 @@ __global__ void k_uf_final(const uint8_t *__restrict__ core, int32_t n, int32_t 
 // or more clusters; -1 for a vertex in no cluster.
 constexpr int32_t kMulti = -2;
 
-// Per non-core vertex: number of eps-similar core neighbours (< mu - 1).
-// Also starts every vertex's membership code from its cid (-1 off cores);
-// union-find is finished, so the parent array is free to hold it.
-__global__ void __launch_bounds__(kBlock) k_border_count(const int64_t *__restrict__ off,
-                                                        const int32_t *__restrict__ adj,
-                                                        const uint8_t *__restrict__ sim,
+// A similar edge with exactly one core endpoint makes the core's cluster a
+// candidate of the other endpoint. Pass 1 counts the candidates per vertex.
+__global__ void __launch_bounds__(kBlock) k_border_count(const int32_t *__restrict__ adj,
+                                                        const int32_t *__restrict__ src,
+                                                        const uint32_t *__restrict__ oe, int64_t m,
+                                                        const uint8_t *__restrict__ simo,
                                                         const uint8_t *__restrict__ core,
-                                                        const int32_t *__restrict__ cid, int32_t *__restrict__ memb,
-                                                        int32_t n, int32_t *__restrict__ cnt) {
-    const int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    int64_t b = 0, e = 0;
-    bool mine = false;  // rows above kHeavy are the heavy kernel's
-    if (v < n) {
-        memb[v] = cid[v];
-        b = off[v];
-        e = off[v + 1];
-        mine = e - b <= kHeavy;
-        if (core[v]) e = b;  // a core has no border candidates
-    }
-    const bool heavy = mine && e - b > kCoop;
-    if (mine && !heavy) {
-        int c = 0;
-        for (int64_t s = b; s < e; ++s)
-            if (sim[s]) c += core[adj[s]];
-        cnt[v] = c;
-    }
-    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
-        const int src = __ffs(hv) - 1;
-        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-        int c = 0;
-        for (int64_t s = hb + lane; s < he; s += kWarp)
-            if (sim[s]) c += core[adj[s]];
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == src) cnt[v] = c;
-    }
+                                                        int32_t *__restrict__ cnt) {
+    for_each_similar(simo, m, [&](int64_t i) {
+        const uint32_t e = oe[i];
+        const int32_t u = src[e], v = adj[e];
+        const uint8_t cu = core[u], cv = core[v];
+        if (cu != cv) atomicAdd(cnt + (cu ? v : u), 1);
+    });
 }
 
-// CTA per heavy vertex: its border candidate count.
-__global__ void __launch_bounds__(kBlock) k_border_count_heavy(const int32_t *__restrict__ heavy,
-                                                              const int64_t *__restrict__ off,
-                                                              const int32_t *__restrict__ adj,
-                                                              const uint8_t *__restrict__ sim,
-                                                              const uint8_t *__restrict__ core,
-                                                              int32_t *__restrict__ cnt) {
-    __shared__ int red[kBlock / 32];
-    const int32_t v = heavy[blockIdx.x];
-    if (core[v]) {
-        if (threadIdx.x == 0) cnt[v] = 0;
-        return;
-    }
-    const int64_t b = off[v], e = off[v + 1];
-    int c = 0;
-    for (int64_t s = b + threadIdx.x; s < e; s += kBlock)
-        if (sim[s]) c += core[adj[s]];
-    c = block_reduce(c, OpAdd(), red);
-    if (threadIdx.x == 0) cnt[v] = c;
+// Pass 2: the same edges write the core's cluster id into the other
+// endpoint's segment [raw_off[x], raw_off[x+1]), in any order, counting
+// cnt[x] back down to zero.
+__global__ void __launch_bounds__(kBlock) k_border_fill(const int32_t *__restrict__ adj,
+                                                       const int32_t *__restrict__ src,
+                                                       const uint32_t *__restrict__ oe, int64_t m,
+                                                       const uint8_t *__restrict__ simo,
+                                                       const uint8_t *__restrict__ core,
+                                                       const int32_t *__restrict__ cid,
+                                                       const int64_t *__restrict__ raw_off, int32_t *cnt,
+                                                       int32_t *__restrict__ raw) {
+    for_each_similar(simo, m, [&](int64_t i) {
+        const uint32_t e = oe[i];
+        const int32_t u = src[e], v = adj[e];
+        const uint8_t cu = core[u], cv = core[v];
+        if (cu == cv) return;
+        const int32_t x = cu ? v : u, y = cu ? u : v;
+        raw[raw_off[x] + atomicSub(cnt + x, 1) - 1] = cid[y];
+    });
 }
 
 // Sorts a[0, k) (k < mu - 1, short) and removes duplicates; returns the
@@ -308,95 +309,36 @@ __device__ __forceinline__ int32_t sort_unique(int32_t *a, int64_t k) {
     return (int32_t)u;
 }
 
-// Per vertex with candidates: the cluster ids of its eps-similar core
-// neighbours, sorted and unique, and its membership code.
-__global__ void __launch_bounds__(kBlock) k_border_fill(const int64_t *__restrict__ off,
-                                                       const int32_t *__restrict__ adj,
-                                                       const uint8_t *__restrict__ sim,
-                                                       const uint8_t *__restrict__ core, int32_t *memb, int32_t n,
-                                                       const int64_t *__restrict__ raw_off, int32_t *__restrict__ raw,
-                                                       int32_t *__restrict__ ucnt) {
+// Per vertex: its candidates sorted and unique (ucnt[v] of them), its
+// membership code, and -- summed over the grid -- the row slots of all
+// vertices in a cluster (the work of the label stage's push direction).
+__global__ void __launch_bounds__(kBlock) k_border_unique(const int64_t *__restrict__ off,
+                                                         const uint8_t *__restrict__ core,
+                                                         const int32_t *__restrict__ cid,
+                                                         const int64_t *__restrict__ raw_off, int32_t n,
+                                                         int32_t *__restrict__ raw, int32_t *__restrict__ ucnt,
+                                                         int32_t *__restrict__ memb,
+                                                         unsigned long long *__restrict__ member_slots) {
+    __shared__ long long red[kBlock / 32];
     const int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    int64_t b = 0, e = 0, base = 0, k = 0;
+    long long slots = 0;
     if (v < n) {
-        base = raw_off[v];
-        k = raw_off[v + 1] - base;
-        if (k > 0) {
-            b = off[v];
-            e = off[v + 1];
-            if (e - b > kHeavy) k = 0, b = e = 0;  // the heavy kernel's
+        int32_t code = -1, uq = 0;
+        if (core[v]) {
+            code = cid[v];
         } else {
-            ucnt[v] = 0;
-        }
-    }
-    const bool heavy = e - b > kCoop;
-    if (k > 0 && !heavy) {
-        int64_t w = base;
-        for (int64_t s = b; s < e; ++s)
-            if (sim[s]) {
-                const int32_t x = adj[s];
-                if (core[x]) raw[w++] = memb[x];  // x is a core: memb is its cid
+            const int64_t b = raw_off[v], k = raw_off[v + 1] - b;
+            if (k > 0) {
+                uq = sort_unique(raw + b, k);
+                code = uq == 1 ? raw[b] : kMulti;
             }
-        const int32_t uq = sort_unique(raw + base, k);
+        }
+        memb[v] = code;
         ucnt[v] = uq;
-        memb[v] = uq == 1 ? raw[base] : kMulti;
+        if (code != -1) slots = off[v + 1] - off[v];
     }
-    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
-        const int src = __ffs(hv) - 1;
-        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-        int64_t w = __shfl_sync(0xffffffffu, base, src);
-        for (int64_t s0 = hb; s0 < he; s0 += kWarp) {
-            const int64_t s = s0 + lane;
-            int32_t x = -1;
-            bool f = false;
-            if (s < he && sim[s]) {
-                const int32_t y = adj[s];
-                if (core[y]) {
-                    f = true;
-                    x = memb[y];
-                }
-            }
-            const unsigned mask = __ballot_sync(0xffffffffu, f);
-            if (f) raw[w + __popc(mask & ((1u << lane) - 1u))] = x;
-            w += __popc(mask);
-        }
-        __syncwarp();
-        if (lane == src) {
-            const int32_t uq = sort_unique(raw + base, k);
-            ucnt[v] = uq;
-            memb[v] = uq == 1 ? raw[base] : kMulti;
-        }
-        __syncwarp();
-    }
-}
-
-// CTA per heavy vertex with candidates: gathered in any order, then sorted.
-__global__ void __launch_bounds__(kBlock) k_border_fill_heavy(const int32_t *__restrict__ heavy,
-                                                             const int64_t *__restrict__ off,
-                                                             const int32_t *__restrict__ adj,
-                                                             const uint8_t *__restrict__ sim,
-                                                             const uint8_t *__restrict__ core, int32_t *memb,
-                                                             const int64_t *__restrict__ raw_off,
-                                                             int32_t *__restrict__ raw, int32_t *__restrict__ ucnt) {
-    __shared__ int32_t fill;
-    const int32_t v = heavy[blockIdx.x];
-    const int64_t base = raw_off[v], k = raw_off[v + 1] - base;
-    if (k == 0) return;  // ucnt[v] = 0 was written by the per-vertex kernel
-    if (threadIdx.x == 0) fill = 0;
-    __syncthreads();
-    const int64_t b = off[v], e = off[v + 1];
-    for (int64_t s = b + threadIdx.x; s < e; s += kBlock)
-        if (sim[s]) {
-            const int32_t y = adj[s];
-            if (core[y]) raw[base + atomicAdd(&fill, 1)] = memb[y];
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int32_t uq = sort_unique(raw + base, k);
-        ucnt[v] = uq;
-        memb[v] = uq == 1 ? raw[base] : kMulti;
-    }
+    slots = block_reduce(slots, OpAdd(), red);
+    if (threadIdx.x == 0 && slots) atomicAdd(member_slots, (unsigned long long)slots);
 }
 
 __global__ void k_border_emit(const int64_t *__restrict__ raw_off, const int32_t *__restrict__ raw,
@@ -416,10 +358,91 @@ __global__ void k_border_emit(const int64_t *__restrict__ raw_off, const int32_t
 // ------------------------------------------------------------------ labels
 // A vertex in no cluster is a hub iff the union of its neighbours'
 // memberships holds two distinct ids: some neighbour is itself in two or
-// more clusters (kMulti), or two neighbours' single ids differ.
+// more clusters (kMulti), or two neighbours' single ids differ. The test
+// runs in whichever direction has fewer row slots to walk: pulled by each
+// vertex in no cluster over its own row, or pushed by each vertex in a
+// cluster to the neighbours in none, which note what they receive in hst:
+// 0 = nothing yet, c + 1 = only cluster c, -1 = two or more (a hub).
+__device__ __forceinline__ bool label_push(const unsigned long long *member_slots, int64_t nnz) {
+    return 2 * (long long)*member_slots <= nnz;
+}
+
+__device__ __forceinline__ void hub_note(int32_t *hst, int32_t u, int32_t code) {
+    if (code == kMulti) {
+        atomicExch(hst + u, -1);
+        return;
+    }
+    const int32_t want = code + 1;
+    int32_t old = hst[u];  // may be stale: it only moves 0 -> c + 1 -> -1
+    if (old == want || old == -1) return;
+    if (old == 0) {
+        old = atomicCAS(hst + u, 0, want);
+        if (old == 0 || old == want || old == -1) return;
+    }
+    atomicExch(hst + u, -1);
+}
+
+// push direction: every vertex in a cluster notes its code at its neighbours in none
+__global__ void __launch_bounds__(kBlock) k_label_push(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                      const int32_t *__restrict__ memb, int32_t n, int64_t nnz,
+                                                      const unsigned long long *__restrict__ member_slots,
+                                                      int32_t *hst) {
+    if (!label_push(member_slots, nnz)) return;
+    const int64_t x = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int64_t b = 0, e = 0;
+    int32_t code = -1;
+    if (x < n) {
+        code = memb[x];
+        if (code != -1) {
+            b = off[x];
+            e = off[x + 1];
+            if (e - b > kHeavy) b = e = 0;  // the heavy kernel's
+        }
+    }
+    const bool heavy = e - b > kCoop;
+    if (!heavy)
+        for (int64_t s = b; s < e; ++s) {
+            const int32_t u = adj[s];
+            if (memb[u] == -1) hub_note(hst, u, code);
+        }
+    for (unsigned hv = __ballot_sync(0xffffffffu, heavy); hv; hv &= hv - 1) {
+        const int src = __ffs(hv) - 1;
+        const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+        const int32_t hc = __shfl_sync(0xffffffffu, code, src);
+        for (int64_t s = hb + lane; s < he; s += kWarp) {
+            const int32_t u = adj[s];
+            if (memb[u] == -1) hub_note(hst, u, hc);
+        }
+    }
+}
+
+// CTA per heavy vertex in a cluster: the push over its whole row.
+__global__ void __launch_bounds__(kBlock) k_label_push_heavy(const int32_t *__restrict__ heavy,
+                                                            const int64_t *__restrict__ off,
+                                                            const int32_t *__restrict__ adj,
+                                                            const int32_t *__restrict__ memb, int64_t nnz,
+                                                            const unsigned long long *__restrict__ member_slots,
+                                                            int32_t *hst) {
+    if (!label_push(member_slots, nnz)) return;
+    const int32_t x = heavy[blockIdx.x];
+    const int32_t code = memb[x];
+    if (code == -1) return;
+    const int64_t b = off[x], e = off[x + 1];
+    for (int64_t s = b + threadIdx.x; s < e; s += kBlock) {
+        const int32_t u = adj[s];
+        if (memb[u] == -1) hub_note(hst, u, code);
+    }
+}
+
+// Every label; in the pull direction a vertex in no cluster walks its row
+// (rows above kHeavy: the heavy kernel), in the push direction it reads hst.
 __global__ void __launch_bounds__(kBlock) k_label(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                                  const uint8_t *__restrict__ core, const int32_t *__restrict__ memb,
-                                                 int32_t n, uint8_t *__restrict__ label) {
+                                                 const int32_t *__restrict__ hst, int32_t n, int64_t nnz,
+                                                 const unsigned long long *__restrict__ member_slots,
+                                                 uint8_t *__restrict__ label) {
+    const bool push = label_push(member_slots, nnz);
     const int64_t u = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int64_t b = 0, e = 0;
@@ -427,6 +450,7 @@ __global__ void __launch_bounds__(kBlock) k_label(const int64_t *__restrict__ of
     if (u < n) {
         if (core[u]) label[u] = SCAN_CORE;
         else if (memb[u] != -1) label[u] = SCAN_BORDER;
+        else if (push) label[u] = hst[u] == -1 ? SCAN_HUB : SCAN_OUTLIER;
         else {
             b = off[u];
             e = off[u + 1];
@@ -484,14 +508,16 @@ __global__ void __launch_bounds__(kBlock) k_label(const int64_t *__restrict__ of
     }
 }
 
-// CTA per heavy vertex in no cluster: hub or outlier over the whole row.
+// CTA per heavy vertex in no cluster (pull direction): hub or outlier over the whole row.
 __global__ void __launch_bounds__(kBlock) k_label_heavy(const int32_t *__restrict__ heavy,
                                                        const int64_t *__restrict__ off,
                                                        const int32_t *__restrict__ adj,
                                                        const uint8_t *__restrict__ core,
-                                                       const int32_t *__restrict__ memb,
+                                                       const int32_t *__restrict__ memb, int64_t nnz,
+                                                       const unsigned long long *__restrict__ member_slots,
                                                        uint8_t *__restrict__ label) {
     __shared__ int red[kBlock / 32];
+    if (label_push(member_slots, nnz)) return;  // labelled from hst by the per-vertex kernel
     const int32_t u = heavy[blockIdx.x];
     if (core[u] || memb[u] != -1) return;  // labelled by the per-vertex kernel
     const int64_t b = off[u], e = off[u + 1];
@@ -582,14 +608,57 @@ static scan_status launch_isect(Graph *g, bool prune, bool write_sim, bool write
     return SCAN_OK;
 }
 
+scan_status cache_reserve(Graph *g) {
+    Ctx *c = g->ctx;
+    const size_t M = (size_t)(g->m > 0 ? g->m : 1);
+    if (!g->cn_cache.ptr) SCAN_TRY(dev_alloc(c, g->cn_cache, sizeof(int32_t) * M));
+    if (!g->cdd.ptr) {
+        const scan_status s = dev_alloc(c, g->cdd, sizeof(uint64_t) * M);
+        if (s != SCAN_OK) {
+            dev_free(c, g->cn_cache);
+            return s;
+        }
+    }
+    return SCAN_OK;
+}
+
+void cache_free(Graph *g) {
+    dev_free(g->ctx, g->cn_cache);
+    dev_free(g->ctx, g->cdd);
+    g->cache_valid = false;
+}
+
 scan_status build_count_cache(Graph *g) {
     Ctx *c = g->ctx;
-    if (!g->cn_cache.ptr) SCAN_TRY(dev_alloc(c, g->cn_cache, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
+    SCAN_TRY(cache_reserve(g));
     int32_t *cn = (int32_t *)g->cn_cache.ptr;
-    if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, cn));
-    else if (g->strategy == SCAN_STRATEGY_BSEARCH) SCAN_TRY(launch_isect(g, false, false, true, QParams{}, cn));
-    else SCAN_TRY(launch_fwd_counts(g, false, true, QParams{}, cn));
+    uint64_t *dd = (uint64_t *)g->cdd.ptr;
+    if (g->strategy == SCAN_STRATEGY_OWNER || g->strategy == SCAN_STRATEGY_BSEARCH) {
+        // per-slot counts into the border scratch (free outside a query's border stage), then oriented
+        int32_t *slot_cn = (int32_t *)g->raw.ptr;
+        if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, slot_cn));
+        else SCAN_TRY(launch_isect(g, false, false, true, QParams{}, slot_cn));
+        if (g->m > 0) {
+            k_cache_orient<<<grid_for(g->m, kBlock, c->num_sms * 32), kBlock, 0, c->stream>>>(
+                (const int32_t *)g->adj.ptr, (const int32_t *)g->src.ptr, (const int32_t *)g->deg.ptr,
+                (const uint32_t *)g->oe.ptr, g->m, slot_cn, cn, dd);
+            c->launches++;
+        }
+    } else {
+        SCAN_TRY(launch_fwd_counts(g, false, true, QParams{}, cn, dd));
+    }
+    SCAN_CUDA(cudaGetLastError());
     g->cache_valid = true;
+    return SCAN_OK;
+}
+
+scan_status cache_to_slots(Graph *g, int32_t *slot_cn) {
+    Ctx *c = g->ctx;
+    if (g->m == 0) return SCAN_OK;
+    k_cache_slots<<<grid_for(g->m, kBlock, c->num_sms * 32), kBlock, 0, c->stream>>>(
+        (const uint32_t *)g->oe.ptr, (const uint32_t *)g->rev.ptr, g->m, (const int32_t *)g->cn_cache.ptr, slot_cn);
+    c->launches++;
+    SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;
 }
 
@@ -602,31 +671,39 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     auto *off = (const int64_t *)g->off.ptr;
     auto *adj = (const int32_t *)g->adj.ptr;
     auto *src = (const int32_t *)g->src.ptr;
-    auto *rev = (const uint32_t *)g->rev.ptr;
     auto *deg = (const int32_t *)g->deg.ptr;
     auto *oe = (const uint32_t *)g->oe.ptr;
     auto *sim = (uint8_t *)g->sim.ptr;
+    auto *simo = (uint8_t *)g->simo.ptr;
+    auto *nsim = (int32_t *)g->nsim.ptr;
     auto *err = (uint32_t *)g->err.ptr;
+    const unsigned gm = grid_for(m, kBlock, c->num_sms * 32);
+    const unsigned gs = grid_for((m + 15) / 16, kBlock, c->num_sms * 32);  // 16 flags per thread
 
     {
         StageTimer t(c, SCAN_STAGE_SIMILARITY);
-        if (nnz > 0) SCAN_CUDA(cudaMemsetAsync(sim, 0, (size_t)nnz, st));
+        if (n > 0) SCAN_CUDA(cudaMemsetAsync(nsim, 0, 4 * (size_t)n, st));
         if (mode & SCAN_Q_BUILD_CACHE) SCAN_TRY(build_count_cache(g));
         const bool use_cache = g->cache_valid && !(mode & (SCAN_Q_RECOMPUTE | SCAN_Q_PLAIN));
         if (use_cache) {
             if (m > 0) {
-                k_sim_from_counts<<<grid_for(m, kBlock, c->num_sms * 32), kBlock, 0, st>>>(
-                    adj, src, rev, deg, oe, m, (const int32_t *)g->cn_cache.ptr, qp, sim);
+                k_sim_from_counts<<<gm, kBlock, 0, st>>>(adj, src, oe, m, (const int32_t *)g->cn_cache.ptr,
+                                                         (const uint64_t *)g->cdd.ptr, qp, simo, nsim);
                 c->launches++;
             }
-        } else if (mode & SCAN_Q_PLAIN) {
-            SCAN_TRY(launch_isect(g, false, true, false, qp, nullptr));
-        } else if (g->strategy == SCAN_STRATEGY_OWNER) {
-            SCAN_TRY(launch_owner_isect(g, true, true, false, qp, nullptr));
-        } else if (g->strategy == SCAN_STRATEGY_BSEARCH) {
-            SCAN_TRY(launch_isect(g, true, true, false, qp, nullptr));
+        } else if (!(mode & SCAN_Q_PLAIN) && g->strategy != SCAN_STRATEGY_OWNER &&
+                   g->strategy != SCAN_STRATEGY_BSEARCH) {
+            SCAN_TRY(launch_fwd_counts(g, true, false, qp, nullptr));  // k_fwd_finish writes simo, nsim
         } else {
-            SCAN_TRY(launch_fwd_counts(g, true, false, qp, nullptr));
+            // the per-edge families write per-slot flags
+            if (nnz > 0) SCAN_CUDA(cudaMemsetAsync(sim, 0, (size_t)nnz, st));
+            if (mode & SCAN_Q_PLAIN) SCAN_TRY(launch_isect(g, false, true, false, qp, nullptr));
+            else if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, true, true, false, qp, nullptr));
+            else SCAN_TRY(launch_isect(g, true, true, false, qp, nullptr));
+            if (m > 0) {
+                k_sim_orient<<<gm, kBlock, 0, st>>>(adj, src, oe, m, sim, simo, nsim);
+                c->launches++;
+            }
         }
     }
 
@@ -641,20 +718,14 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     const unsigned gt = grid_for(n, kBlock);
     {
         StageTimer t(c, SCAN_STAGE_CORE);
-        k_core<<<gt, kBlock, 0, st>>>(off, sim, n, qp, core);
+        k_core<<<gt, kBlock, 0, st>>>(nsim, n, qp, core);
         c->launches++;
-        if (nh > 0) {
-            k_core_heavy<<<nh, kBlock, 0, st>>>(heavy, off, sim, qp, core);
-            c->launches++;
-        }
     }
     {
         StageTimer t(c, SCAN_STAGE_CLUSTER);
         int32_t *parent = (int32_t *)g->parent.ptr;
         k_uf_init<<<gt, kBlock, 0, st>>>(core, n, parent);
-        if (m > 0)
-            k_uf_hook<<<grid_for(m, kBlock, c->num_sms * 32), kBlock, 0, st>>>(adj, src, oe, m, sim, core, parent,
-                                                                                err);
+        if (m > 0) k_uf_hook<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, parent, err);
         k_uf_final<<<gt, kBlock, 0, st>>>(core, n, parent, cid, err);
         c->launches += 2 + (m > 0);
     }
@@ -664,31 +735,40 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     int64_t *pair_off = (int64_t *)g->pair_off.ptr;
     int32_t *raw = (int32_t *)g->raw.ptr;
     int32_t *memb = (int32_t *)g->parent.ptr;  // membership codes once union-find is done
+    auto *mslots = (unsigned long long *)g->mslots.ptr;
     {
         StageTimer t(c, SCAN_STAGE_BORDER);
-        k_border_count<<<gt, kBlock, 0, st>>>(off, adj, sim, core, cid, memb, n, cnt);
-        c->launches++;
-        if (nh > 0) {
-            k_border_count_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, sim, core, cnt);
+        SCAN_CUDA(cudaMemsetAsync(cnt, 0, 4 * (size_t)n, st));
+        SCAN_CUDA(cudaMemsetAsync(mslots, 0, sizeof(unsigned long long), st));
+        if (m > 0) {
+            k_border_count<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, cnt);
             c->launches++;
         }
         SCAN_TRY(launch_exclusive_scan_i32_to_i64(c, cnt, cnt_off, n, g->scan_tmp));
-        k_border_fill<<<gt, kBlock, 0, st>>>(off, adj, sim, core, memb, n, cnt_off, raw, ucnt);
-        c->launches++;
-        if (nh > 0) {
-            k_border_fill_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, sim, core, memb, cnt_off, raw, ucnt);
+        if (m > 0) {
+            k_border_fill<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, cid, cnt_off, cnt, raw);
             c->launches++;
         }
+        k_border_unique<<<gt, kBlock, 0, st>>>(off, core, cid, cnt_off, n, raw, ucnt, memb, mslots);
+        c->launches++;
         SCAN_TRY(launch_exclusive_scan_i32_to_i64(c, ucnt, pair_off, n, g->scan_tmp));
         k_border_emit<<<gt, kBlock, 0, st>>>(cnt_off, raw, ucnt, pair_off, n, pairs, pairs_cap, npairs);
         c->launches++;
     }
     {
         StageTimer t(c, SCAN_STAGE_LABEL);
-        k_label<<<gt, kBlock, 0, st>>>(off, adj, core, memb, n, label);
+        int32_t *hst = (int32_t *)g->hst.ptr;
+        SCAN_CUDA(cudaMemsetAsync(hst, 0, 4 * (size_t)n, st));
+        k_label_push<<<gt, kBlock, 0, st>>>(off, adj, memb, n, nnz, mslots, hst);
         c->launches++;
         if (nh > 0) {
-            k_label_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, core, memb, label);
+            k_label_push_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, memb, nnz, mslots, hst);
+            c->launches++;
+        }
+        k_label<<<gt, kBlock, 0, st>>>(off, adj, core, memb, hst, n, nnz, mslots, label);
+        c->launches++;
+        if (nh > 0) {
+            k_label_heavy<<<nh, kBlock, 0, st>>>(heavy, off, adj, core, memb, nnz, mslots, label);
             c->launches++;
         }
     }

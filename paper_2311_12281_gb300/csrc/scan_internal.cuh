@@ -47,7 +47,8 @@ struct Graph {
     int64_t nnz = 0;
     int64_t m = 0;          // undirected edges = nnz / 2
     DevBuf off, adj, src, rev, deg, oe;
-    DevBuf cn_cache;        // int32[nnz] closed common counts (cached-count serving)
+    DevBuf cn_cache;        // int32[m] closed common counts per oriented edge (cached-count serving)
+    DevBuf cdd;             // uint64[m] (deg u + 1)(deg v + 1) per oriented edge (same cache)
     bool cache_valid = false;
     // owner schedule of the shared-memory intersection (built on first use)
     bool owner_ready = false;
@@ -87,7 +88,11 @@ struct Graph {
     bool heavy_ready = false;
     Part *part = nullptr;   // non-null: the CSR stays in host memory and is streamed in blocks
     // per-query scratch
-    DevBuf sim;             // uint8[nnz] 1 = eps-similar
+    DevBuf sim;             // uint8[nnz] 1 = eps-similar (per-slot output of the per-edge families)
+    DevBuf simo;            // uint8[m] 1 = oriented edge oe[i] is eps-similar
+    DevBuf nsim;            // int32[n+1] open eps-degree
+    DevBuf hst;             // int32[n+1] hub test state of the label stage's push direction
+    DevBuf mslots;          // uint64[1] row slots of the vertices in a cluster
     DevBuf core, cid, parent, label;
     DevBuf cnt, cnt_off;    // int32[n+1] counts, int64[n+1] exclusive offsets
     DevBuf ucnt, pair_off;  // unique membership counts / offsets
@@ -102,10 +107,10 @@ struct Graph {
 
     template <class F>
     void for_each_buf(F f) {
-        DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &owners_small, &items[0], &items[1],
+        DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &cdd, &owners_small, &items[0], &items[1],
                           &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
                           &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
-                          &qparams, &sim, &core, &cid, &parent, &label,
+                          &qparams, &sim, &simo, &nsim, &hst, &mslots, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
         for (DevBuf *b : bufs) f(*b);
     }
@@ -243,11 +248,19 @@ scan_status query_replay(Graph *g, const scan_params &p, uint32_t mode, uint8_t 
 void query_graph_drop(Graph *g);  // forget the captured graph (buffers or kernel choice changed)
 uint64_t replay_key(uint32_t mode, const void *a, const void *b, const void *c, const void *d, int64_t cap,
                     const void *e);  // identity of a captured launch sequence
+// The count cache: per oriented edge oe[i], its closed common count and the
+// product of its endpoints' closed degrees, so that a cached query's eps-test
+// reads 12 contiguous bytes per edge and no vertex data.
+scan_status cache_reserve(Graph *g);  // allocate both arrays (no-op when present)
+void cache_free(Graph *g);            // free them; the cache is no longer valid
 scan_status build_count_cache(Graph *g);
+scan_status cache_to_slots(Graph *g, int32_t *slot_counts);  // int32[nnz] device, counts per slot
 scan_status owner_schedule_build(Graph *g);
 scan_status launch_owner_isect(Graph *g, bool prune, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);
 scan_status fwd_prepare(Graph *g);
-scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn);
+// write_cn: cn[i] and dd[i] of every oriented edge (the count cache)
+scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn,
+                              uint64_t *dd = nullptr);
 
 inline QParams uniform_params(const scan_params &p) {
     QParams q;
@@ -276,6 +289,10 @@ __device__ __forceinline__ bool eps_similar(uint64_t c, uint64_t du1, uint64_t d
     unsigned __int128 lhs = (unsigned __int128)(c * c) * qq;
     unsigned __int128 rhs = (unsigned __int128)pp * (du1 * dv1);
     return lhs >= rhs;
+}
+// the same test on the product dd = du1 * dv1
+__device__ __forceinline__ bool eps_similar_dd(uint64_t c, uint64_t dd, uint64_t pp, uint64_t qq) {
+    return (unsigned __int128)(c * c) * qq >= (unsigned __int128)pp * dd;
 }
 
 // Degree-only outcomes (|N[u] cap N[v]| lies in [2, min(du, dv)]):

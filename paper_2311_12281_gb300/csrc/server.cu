@@ -133,8 +133,7 @@ struct scan_server {
                 best = &sg;
         if (best) {
             query_graph_drop(best->g);
-            dev_free(ctx, best->g->cn_cache);
-            best->g->cache_valid = false;
+            cache_free(best->g);
             std::lock_guard<std::mutex> lock(mu);
             ++cache_evictions;
             return true;
@@ -216,7 +215,7 @@ struct scan_server {
                 // reserve the cache up front; without room the query recomputes
                 bool ok = false;
                 for (int attempt = 0; attempt < 1 << 20 && !ok; ++attempt) {
-                    scan_status a = dev_alloc(ctx, g->cn_cache, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1));
+                    scan_status a = cache_reserve(g);
                     if (a == SCAN_OK) ok = true;
                     else if (!evict_one(&sg)) break;
                 }
