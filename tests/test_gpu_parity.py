@@ -195,6 +195,49 @@ def test_autotune_keeps_results_exact_and_persists(ps, ctx, tmp_path):
         dg.free()
 
 
+def member_slots(graph, res):
+    """Row slots of the vertices in a cluster (cores and borders)."""
+    lab = np.asarray(res["label"])
+    return int(graph.degrees()[(lab == 0) | (lab == 1)].sum())
+
+
+@pytest.mark.parametrize("leaves", [1, 200])
+def test_hub_through_a_neighbour_in_two_clusters(ps, ctx, leaves):
+    # two 5-cliques; x touches two vertices of each, so at eps = 1/2, mu = 6
+    # those four are cores, x is a border of both clusters, and h (adjacent to
+    # x and to `leaves` pendant vertices, so not similar to x) is a hub only
+    # through x. With one leaf the vertices in a cluster hold most row slots
+    # and the label stage pulls; with many it pushes. Either way h must be the
+    # oracle's hub.
+    a, b, x, h = list(range(5)), list(range(5, 10)), 10, 11
+    edges = [(i, j) for grp in (a, b) for i in grp for j in grp if i < j]
+    edges += [(x, 0), (x, 1), (x, 5), (x, 6), (x, h)]
+    edges += [(h, 12 + k) for k in range(leaves)]
+    g = gg.from_edges(12 + leaves, edges)
+    g.name = f"two cliques, multi-border, {leaves} leaves"
+    want = oracle.scan(g, 1, 2, 6)
+    assert want["label"][h] == ps.SCAN_HUB and want["label"][x] == ps.SCAN_BORDER
+    pushes = 2 * member_slots(g, want) <= g.nnz
+    assert pushes == (leaves > 10)
+    check_graph(ps, ctx, g, [(1, 2, 6)])
+
+
+def test_hub_test_directions_on_power_law_graphs(ps, ctx):
+    # low eps: most slots belong to clustered vertices (pull); high eps: few (push)
+    g = gg.rmat(13, 16, seed=21)
+    seen = set()
+    dg = ctx.load(g)
+    try:
+        for (p, q, mu) in [(1, 5, 2), (1, 5, 5), (3, 10, 3), (1, 2, 3), (7, 10, 2), (4, 5, 2)]:
+            want = oracle.scan(g, p, q, mu)
+            seen.add(2 * member_slots(g, want) <= g.nnz)
+            for mode in MODES:
+                assert_same(gpu_query(ps, dg, p, q, mu, mode), want, f"{g.name} eps={p}/{q} mu={mu} mode={mode}")
+    finally:
+        dg.free()
+    assert seen == {True, False}
+
+
 def test_query_entry_points_agree(ps, ctx):
     g = gg.rmat(12, 16, seed=9)
     dg = ctx.load(g)
