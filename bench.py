@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -333,7 +334,21 @@ def run_serving(args):
     def run(srv, ids, reqs, rate, max_wall_s):
         gaps = rng.exponential(1.0 / rate, len(reqs))
         ps.scan_server_reset_stats(srv)
-        tickets = []
+        # clients take their answers as they complete (a consumer thread that
+        # releases each result), so result memory is recycled as it would be
+        # in service
+        pending = queue.Queue()
+
+        def consume():
+            while True:
+                tk = pending.get()
+                if tk is None:
+                    return
+                ps.scan_server_wait(srv, tk, keep=False)
+
+        consumer = threading.Thread(target=consume)
+        consumer.start()
+        submitted = 0
         t_start = time.perf_counter()
         due = t_start
         for gap, (gi, p, q, mu) in zip(gaps, reqs):
@@ -344,13 +359,14 @@ def run_serving(args):
                     break
                 if due - now > 2e-4:
                     time.sleep(min(due - now - 1e-4, 0.01))
-            tickets.append(ps.scan_server_submit(srv, ids[gi], p, q, mu))
+            pending.put(ps.scan_server_submit(srv, ids[gi], p, q, mu))
+            submitted += 1
             if time.perf_counter() - t_start > max_wall_s:
                 break
-        for tk in tickets:
-            ps.scan_server_wait(srv, tk)
+        pending.put(None)
+        consumer.join()
         st = ps.scan_server_stats(srv)
-        st["submitted"] = len(tickets)
+        st["submitted"] = submitted
         return st
 
     out = {}

@@ -397,10 +397,14 @@ def scan_server_submit(srv: int, graph_id: int, eps_num: int, eps_den: int, mu: 
     return t.value
 
 
-def scan_server_wait(srv: int, ticket: int) -> tuple[dict, float]:
+def scan_server_wait(srv: int, ticket: int, keep: bool = True) -> tuple[dict | None, float]:
+    """(result, latency_ms); with keep=False the result is released unread (None)."""
     out = ctypes.c_void_p()
     lat = ctypes.c_double()
     _check(lib().scan_server_wait(srv, ctypes.c_uint64(ticket), ctypes.byref(out), ctypes.byref(lat)))
+    if not keep:
+        lib().scan_result_free(out.value)
+        return None, lat.value
     return _result_to_numpy(out.value), lat.value
 
 

@@ -354,6 +354,23 @@ scan_result *result_new(int32_t n, int64_t k, bool pinned) {
     return r;
 }
 
+bool result_set_pairs(scan_result *r, int64_t k) {
+    const size_t bk = 8 * (size_t)k + 8;
+    if (r->pinned) {
+        if (bk > r->cap[3]) {
+            pinned_put(r->pairs, r->cap[3]);
+            r->pairs = (int32_t *)pinned_get(bk, &r->cap[3]);
+        }
+    } else {
+        void *p = realloc(r->pairs, bk);
+        if (p) r->pairs = (int32_t *)p;
+        else return false;
+    }
+    if (!r->pairs) return false;
+    r->k = k;
+    return true;
+}
+
 }  // namespace scan
 
 extern "C" {

@@ -216,6 +216,7 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
                          Graph **out);
 void graph_destroy(Graph *g);
 scan_result *result_new(int32_t n, int64_t k, bool pinned);
+bool result_set_pairs(scan_result *r, int64_t k);  // room for k pairs (r->k = k); false if out of memory
 // out of core (partition.cu)
 scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, Graph **out,
                         int64_t block_slots_hint);

@@ -71,11 +71,9 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     int state = 0;  // 0 idle, 1 arrays in flight, 2 border pairs in flight
     Request req;
-    uint8_t *h_core = nullptr, *h_label = nullptr;
-    int32_t *h_cid = nullptr, *h_pairs = nullptr;
+    scan_result *res = nullptr;  // the answer, copied from the device straight into its pinned blocks
     int64_t *h_np = nullptr;
     uint32_t *h_err = nullptr;
-    size_t cap_n = 0, cap_pairs = 0;
 };
 
 // Points the context's launch stream at `s` for the lifetime of the guard
@@ -172,29 +170,6 @@ struct scan_server {
         return SCAN_EBUDGET;
     }
 
-    bool grow_staging(Slot &sl, size_t n, size_t pairs) {
-        if (n > sl.cap_n) {
-            if (sl.h_core) cudaFreeHost(sl.h_core);
-            if (sl.h_label) cudaFreeHost(sl.h_label);
-            if (sl.h_cid) cudaFreeHost(sl.h_cid);
-            sl.h_core = sl.h_label = nullptr;
-            sl.h_cid = nullptr;
-            sl.cap_n = 0;
-            if (cudaMallocHost(&sl.h_core, n) != cudaSuccess || cudaMallocHost(&sl.h_label, n) != cudaSuccess ||
-                cudaMallocHost(&sl.h_cid, 4 * n) != cudaSuccess)
-                return false;
-            sl.cap_n = n;
-        }
-        if (pairs > sl.cap_pairs) {
-            if (sl.h_pairs) cudaFreeHost(sl.h_pairs);
-            sl.h_pairs = nullptr;
-            sl.cap_pairs = 0;
-            if (cudaMallocHost(&sl.h_pairs, 8 * pairs) != cudaSuccess) return false;
-            sl.cap_pairs = pairs;
-        }
-        return true;
-    }
-
     // Launch one request on a free slot. Returns false if it must wait.
     bool admit(const Request &rq, Slot &sl) {
         SrvGraph &sg = graphs[(size_t)rq.gid];
@@ -226,8 +201,11 @@ struct scan_server {
                 }
             }
         }
-        if (!grow_staging(sl, (size_t)g->n + 1, 0)) {
-            finish(rq, nullptr, SCAN_ENOMEM, "pinned staging allocation failed");
+        // the result's arrays come from the pinned block pool, so the device
+        // writes them directly and the worker never copies a result on the host
+        sl.res = result_new(g->n, 0, true);
+        if (!sl.res) {
+            finish(rq, nullptr, SCAN_ENOMEM, "pinned result allocation failed");
             return true;
         }
         {
@@ -238,16 +216,20 @@ struct scan_server {
             if (s == SCAN_OK) e = cudaMemcpyAsync(sl.h_np, g->npairs.ptr, 8, cudaMemcpyDeviceToHost, sl.stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, g->err.ptr, 4, cudaMemcpyDeviceToHost, sl.stream);
             if (e == cudaSuccess && g->n > 0) {
-                e = cudaMemcpyAsync(sl.h_core, g->core.ptr, (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
+                scan_result *r = sl.res;
+                e = cudaMemcpyAsync(r->core, g->core.ptr, (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(sl.h_cid, g->cid.ptr, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
+                    e = cudaMemcpyAsync(r->cid, g->cid.ptr, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(sl.h_label, g->label.ptr, (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
+                    e = cudaMemcpyAsync(r->label, g->label.ptr, (size_t)g->n, cudaMemcpyDeviceToHost, sl.stream);
             }
             if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
             if (s == SCAN_OK && e != cudaSuccess) s = cuda_fail(e, "server launch");
         }
         if (s != SCAN_OK) {
+            cudaStreamSynchronize(sl.stream);  // copies into the result may be queued
+            scan_result_free(sl.res);
+            sl.res = nullptr;
             finish(rq, nullptr, s, "query launch failed");
             return true;
         }
@@ -263,6 +245,8 @@ struct scan_server {
 
     void release_slot(Slot &sl) {
         graphs[(size_t)sl.req.gid].busy = false;
+        scan_result_free(sl.res);  // null once handed to the caller
+        sl.res = nullptr;
         sl.state = 0;
         std::lock_guard<std::mutex> lock(mu);
         --inflight;
@@ -283,30 +267,20 @@ struct scan_server {
             if (g->cache_valid == false && g->cn_cache.ptr) g->cache_valid = true;
             const int64_t k = *sl.h_np;
             if (k > 0) {
-                if (!grow_staging(sl, 0, (size_t)k)) {
-                    finish(sl.req, nullptr, SCAN_ENOMEM, "pinned staging allocation failed");
+                if (!result_set_pairs(sl.res, k)) {
+                    finish(sl.req, nullptr, SCAN_ENOMEM, "pinned result allocation failed");
                     release_slot(sl);
                     return;
                 }
-                cudaMemcpyAsync(sl.h_pairs, g->pairs.ptr, 8 * (size_t)k, cudaMemcpyDeviceToHost, sl.stream);
+                cudaMemcpyAsync(sl.res->pairs, g->pairs.ptr, 8 * (size_t)k, cudaMemcpyDeviceToHost, sl.stream);
                 cudaEventRecord(sl.ev, sl.stream);
                 sl.state = 2;
                 return;
             }
         }
-        const int64_t k = *sl.h_np;
-        scan_result *r = result_new(g->n, k, false);
-        if (!r) {
-            finish(sl.req, nullptr, SCAN_ENOMEM, "result allocation failed");
-        } else {
-            if (g->n > 0) {
-                memcpy(r->core, sl.h_core, (size_t)g->n);
-                memcpy(r->cid, sl.h_cid, 4 * (size_t)g->n);
-                memcpy(r->label, sl.h_label, (size_t)g->n);
-            }
-            if (k > 0) memcpy(r->pairs, sl.h_pairs, 8 * (size_t)k);
-            finish(sl.req, r, SCAN_OK, "");
-        }
+        scan_result *r = sl.res;
+        sl.res = nullptr;
+        finish(sl.req, r, SCAN_OK, "");
         release_slot(sl);
     }
 
@@ -544,7 +518,8 @@ void scan_server_destroy(scan_server *s) {
         for (cudaStream_t st : {sl.hi, sl.lo})
             if (st) cudaStreamSynchronize(st), cudaStreamDestroy(st);
         if (sl.ev) cudaEventDestroy(sl.ev);
-        void *pin[] = {sl.h_core, sl.h_label, sl.h_cid, sl.h_pairs, sl.h_np, sl.h_err};
+        scan_result_free(sl.res);
+        void *pin[] = {sl.h_np, sl.h_err};
         for (void *p : pin)
             if (p) cudaFreeHost(p);
     }
