@@ -795,14 +795,13 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
 // closed-degree product) or the eps-test (a flag per oriented edge and the
 // endpoints' eps-degrees)
 template <bool WRITE_SIM, bool WRITE_CN>
-__global__ void k_fwd_finish(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ fcnt,
-                             const int32_t *__restrict__ src, const int32_t *__restrict__ adj,
-                             const int32_t *__restrict__ deg, QParams qp, uint8_t *__restrict__ simo,
-                             int32_t *__restrict__ nsim, int32_t *__restrict__ cn, uint64_t *__restrict__ dd) {
+__global__ void k_fwd_finish(int64_t m, const int32_t *__restrict__ fcnt, const int32_t *__restrict__ fsrc,
+                             const int32_t *__restrict__ fadj, const int32_t *__restrict__ deg, QParams qp,
+                             uint8_t *__restrict__ simo, int32_t *__restrict__ nsim, int32_t *__restrict__ cn,
+                             uint64_t *__restrict__ dd) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t e = oe[i];
         const int32_t c = fcnt[i] + 2;
-        const int32_t u = src[e], v = adj[e];
+        const int32_t u = fsrc[i], v = fadj[i];
         if (WRITE_CN) {
             cn[i] = c;
             dd[i] = ((uint64_t)deg[u] + 1) * ((uint64_t)deg[v] + 1);
@@ -919,9 +918,16 @@ __global__ void k_fwd_adj(const uint32_t *__restrict__ oe, int64_t m, const int3
     }
 }
 
-// CTA item classes by the owner's out-degree: 0 up to 256 (256-thread CTAs,
-// 16.5 KB tables), 1 up to 1024 (512 threads, 64.5 KB), 2 above (512
-// threads, tables of 4096-key chunks, 128.5 KB)
+// lower endpoint of every oriented edge, in fadj order (once the lists are final)
+__global__ void k_fwd_src(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ src,
+                          int32_t *__restrict__ fsrc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        fsrc[i] = src[oe[i]];
+}
+
+// CTA item classes by the owner's out-degree: 0 up to 256 (128-thread CTAs,
+// 8 KB tables), 1 up to 1024 (512 threads, 32 KB), 2 above (512 threads,
+// tables of 4096-key chunks, 128 KB)
 __host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
 
 // warp per vertex: work as a middle vertex and the number of items
@@ -1132,10 +1138,12 @@ scan_status fwd_prepare(Graph *g) {
         scan_status s = dev_alloc(c, g->fadj, 4 * (size_t)m);
         if (s == SCAN_OK) s = dev_alloc(c, g->fin, 4 * (size_t)g->nnz);
         if (s == SCAN_OK) s = dev_alloc(c, g->fcnt, 4 * (size_t)m);
+        if (s == SCAN_OK) s = dev_alloc(c, g->fsrc, 4 * (size_t)m);
         if (s != SCAN_OK) {
             dev_free(c, g->fadj);
             dev_free(c, g->fin);
             dev_free(c, g->fcnt);
+            dev_free(c, g->fsrc);
             dev_free(c, cnts);
             return s;
         }
@@ -1165,6 +1173,9 @@ scan_status fwd_prepare(Graph *g) {
                 (const uint32_t *)g->oe.ptr, m, (const uint32_t *)g->rev.ptr, (uint32_t *)g->fin.ptr);
             c->launches += 2 + (h2[0] > 0);
         }
+        k_fwd_src<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
+            (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->src.ptr, (int32_t *)g->fsrc.ptr);
+        c->launches++;
     }
     // schedule (rebuilt alone when the autotuner changes its parameters)
     SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
@@ -1227,19 +1238,20 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
         for (int cls = 2; cls >= 0; --cls) {
             const int64_t ni = g->fwd_items_n[cls];
             if (ni == 0) continue;
-            // up to eight slots per key (load 1/8): class 0 always, class 1 up to
-            // 512 keys (4 slots per key above: the 32 KB table lets four
-            // 512-thread CTAs share an SM), class 2 four per key; 8 bytes per
-            // slot (key + count): 16 KB, 32 KB, 128 KB
-            const int cap_logs = cls == 0 ? 11 : (cls == 1 ? 12 : 14), load_shift = cls == 2 ? 2 : 3;
+            // 8 bytes per slot (key + count). Class 0: four slots per key, 8 KB,
+            // 128-thread CTAs (sixteen per SM: these owners hold little work,
+            // and small CTAs wait less at their barriers). Class 1: eight slots
+            // per key up to 512 keys, four above, 32 KB (four 512-thread CTAs
+            // per SM). Class 2: four per key, 128 KB.
+            const int cap_logs = cls == 0 ? 10 : (cls == 1 ? 12 : 14), load_shift = cls == 1 ? 3 : 2;
             const size_t smem = (size_t)(2 * sizeof(int)) << cap_logs;
             auto *items = (const FItem *)g->fwd_items[cls].ptr;
             auto *eb = (const int32_t *)g->fwd_ebase.ptr;
             auto *el = (const int32_t *)g->fwd_elen.ptr;
             auto *ef = (const uint32_t *)g->fwd_efin.ptr;
             if (cls == 0) {
-                SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
+                SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_fwd_ent<128><<<(unsigned)ni, 128, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
                                                                 load_shift);
             } else {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1268,16 +1280,15 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
         c->launches++;
     }
     const unsigned gf = grid_for(g->m, 256, c->num_sms * 32);
-    auto *oe = (const uint32_t *)g->oe.ptr;
-    auto *src = (const int32_t *)g->src.ptr;
+    auto *fsrc = (const int32_t *)g->fsrc.ptr;
     auto *simo = (uint8_t *)g->simo.ptr;
     auto *nsim = (int32_t *)g->nsim.ptr;
     if (write_sim && write_cn)
-        k_fwd_finish<true, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
+        k_fwd_finish<true, true><<<gf, 256, 0, st>>>(g->m, fcnt, fsrc, fadj, deg, qp, simo, nsim, cn, dd);
     else if (write_cn)
-        k_fwd_finish<false, true><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
+        k_fwd_finish<false, true><<<gf, 256, 0, st>>>(g->m, fcnt, fsrc, fadj, deg, qp, simo, nsim, cn, dd);
     else
-        k_fwd_finish<true, false><<<gf, 256, 0, st>>>(oe, g->m, fcnt, src, adj, deg, qp, simo, nsim, cn, dd);
+        k_fwd_finish<true, false><<<gf, 256, 0, st>>>(g->m, fcnt, fsrc, fadj, deg, qp, simo, nsim, cn, dd);
     c->launches++;
     SCAN_CUDA(cudaGetLastError());
     return SCAN_OK;

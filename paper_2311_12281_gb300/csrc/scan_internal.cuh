@@ -64,6 +64,7 @@ struct Graph {
     DevBuf fadj;            // int32[m] out(x) neighbour ids, ascending
     DevBuf fin;             // uint32[nnz] for a slot (b, a) with a below b: index of a->b in fadj
     DevBuf fcnt;            // int32[m] triangle counts per oriented edge
+    DevBuf fsrc;            // int32[m] lower endpoint of each oriented edge, in fadj order
     DevBuf fwd_owners;      // warp-level owners
     DevBuf fwd_items[3];    // CTA items, by table class 1..2
     int64_t fwd_items_n[3] = {0, 0, 0};
@@ -108,7 +109,7 @@ struct Graph {
     template <class F>
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &cdd, &owners_small, &items[0], &items[1],
-                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fwd_owners,
+                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fwd_owners,
                           &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
                           &qparams, &sim, &simo, &nsim, &hst, &mslots, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
