@@ -114,7 +114,9 @@ SCAN_API scan_status scan_ctx_stage_time(scan_ctx *ctx, int32_t stage, double *t
  * Requirements (checked on the device; nothing is repaired): each row sorted
  * strictly ascending (so no duplicates), ids in [0, n), no self-loops, and
  * symmetric (v in row u <=> u in row v). Violations: SCAN_EINVAL with the
- * first bad slot in scan_last_error(). n = 0 is valid.
+ * first bad slot in scan_last_error(); when every slot pointing to a higher
+ * id has its reverse and the graph is still not symmetric, the numbers of
+ * slots pointing to higher and to lower ids instead. n = 0 is valid.
  *
  * Without SCAN_LOAD_PINNED_BORROW the library copies the arrays to the
  * device and the caller may release them on return. If the graph's device

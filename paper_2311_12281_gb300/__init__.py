@@ -269,25 +269,44 @@ def scan_graph_copy_counts(g: int, nnz: int) -> np.ndarray:
     return out[:nnz]
 
 
+class _ResultOwner:
+    """Holds one scan_result; it is freed when the last array viewing it goes."""
+
+    __slots__ = ("r",)
+
+    def __init__(self, r: int):
+        self.r = r
+
+    def __del__(self):
+        if self.r:
+            try:
+                lib().scan_result_free(self.r)
+            except Exception:  # interpreter shutdown: the process frees it
+                pass
+            self.r = None
+
+
 def _result_to_numpy(r: int) -> dict:
+    """The result's arrays as numpy views of its own (pinned) buffers: no host
+    copy; the result is released once every array is gone."""
     L = lib()
     n = L.scan_result_n(r)
     k = L.scan_result_border_count(r)
+    owner = _ResultOwner(r)
 
     def arr(ptr, dtype, count):
         if count == 0:
             return np.zeros(0, dtype=dtype)
         buf = (ctypes.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
-        return np.frombuffer(buf, dtype=dtype, count=count).copy()
+        buf._owner = owner  # the view's base keeps the result alive
+        return np.frombuffer(buf, dtype=dtype, count=count)
 
-    out = {
+    return {
         "core": arr(L.scan_result_core(r), np.uint8, n),
         "cid": arr(L.scan_result_cluster(r), np.int32, n),
         "label": arr(L.scan_result_label(r), np.uint8, n),
         "pairs": arr(L.scan_result_border_pairs(r), np.int32, 2 * k).reshape(k, 2),
     }
-    L.scan_result_free(r)
-    return out
 
 
 def scan_query(g: int, eps_num: int, eps_den: int, mu: int) -> dict:

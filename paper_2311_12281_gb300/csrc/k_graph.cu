@@ -36,29 +36,43 @@ __global__ void k_deg_src(const int64_t *__restrict__ off, int32_t n, int32_t *_
     for (int64_t s = b + lane; s < e; s += kWarp) src[s] = (int32_t)u;
 }
 
-// slot checks + reverse slot by binary search of u in row v
+// Slot checks, and for each slot (u, v) with u < v the position of u in row
+// v by binary search: the reverse slot of both. Each such slot finds a
+// distinct partner with a smaller id, so once every one has found it and the
+// two kinds are equally many (counted in `up`), every slot is matched.
 __global__ void k_check_rev(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                             const int32_t *__restrict__ src, int32_t n, int64_t nnz, uint32_t *__restrict__ rev,
-                            unsigned long long *bad) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nnz) return;
-    int32_t u = src[s], v = adj[s];
-    bool ok = v >= 0 && v < n && v != u;
-    if (ok && s > off[u]) ok = adj[s - 1] < v;
-    if (ok) {
-        int64_t lo = off[v], hi = off[v + 1];
-        int64_t found = -1;
-        for (int it = 0; it < 64 && lo < hi; ++it) {
-            int64_t mid = lo + ((hi - lo) >> 1);
-            int32_t x = adj[mid];
-            if (x < u) lo = mid + 1;
-            else if (x > u) hi = mid;
-            else { found = mid; break; }
+                            unsigned long long *bad, unsigned long long *up) {
+    __shared__ unsigned int block_up;
+    if (threadIdx.x == 0) block_up = 0;
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nnz) {
+        const int32_t u = src[s], v = adj[s];
+        bool ok = v >= 0 && v < n && v != u;
+        if (ok && s > off[u]) ok = adj[s - 1] < v;
+        if (ok && v > u) {
+            atomicAdd(&block_up, 1u);
+            int64_t lo = off[v], hi = off[v + 1];
+            int64_t found = -1;
+            for (int it = 0; it < 64 && lo < hi; ++it) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                const int32_t x = adj[mid];
+                if (x < u) lo = mid + 1;
+                else if (x > u) hi = mid;
+                else { found = mid; break; }
+            }
+            if (found < 0) {
+                ok = false;
+            } else {
+                rev[s] = (uint32_t)found;
+                rev[found] = (uint32_t)s;
+            }
         }
-        if (found < 0) ok = false;
-        else rev[s] = (uint32_t)found;
+        if (!ok) atomicMin(bad, (unsigned long long)s);
     }
-    if (!ok) atomicMin(bad, (unsigned long long)s);
+    __syncthreads();
+    if (threadIdx.x == 0 && block_up) atomicAdd(up, (unsigned long long)block_up);
 }
 
 // per vertex: number of slots whose neighbour ranks above it
@@ -107,11 +121,12 @@ scan_status graph_prepare(Graph *g) {
     const int32_t n = g->n;
     const int64_t nnz = g->nnz;
     DevBuf badb;
-    SCAN_TRY(dev_alloc(c, badb, sizeof(unsigned long long)));
-    unsigned long long *bad = (unsigned long long *)badb.ptr;
-    unsigned long long hbad = kNoBad;
+    SCAN_TRY(dev_alloc(c, badb, 2 * sizeof(unsigned long long)));
+    unsigned long long *bad = (unsigned long long *)badb.ptr, *up = bad + 1;
+    unsigned long long hbad = kNoBad, hup = 0;
     auto fail = [&](scan_status s) { dev_free(c, badb); return s; };
     cudaError_t e = cudaMemcpyAsync(bad, &hbad, sizeof(hbad), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(up, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "upload bad flag"));
 
     const int64_t *off = (const int64_t *)g->off.ptr;
@@ -135,15 +150,21 @@ scan_status graph_prepare(Graph *g) {
         c->launches++;
     }
     if (nnz > 0) {
-        k_check_rev<<<grid_for(nnz, 256), 256, 0, c->stream>>>(off, adj, src, n, nnz, rev, bad);
+        k_check_rev<<<grid_for(nnz, 256), 256, 0, c->stream>>>(off, adj, src, n, nnz, rev, bad, up);
         c->launches++;
     }
     e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hup, up, sizeof(hup), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "slot checks"));
     if (hbad != kNoBad) {
         set_error("invalid CSR at slot " + std::to_string(hbad) +
                   " (rows must be strictly ascending, ids in [0, n), no self-loops, symmetric)");
+        return fail(SCAN_EINVAL);
+    }
+    if (2 * hup != (unsigned long long)nnz) {
+        set_error("invalid CSR: not symmetric (" + std::to_string(hup) + " slots point to a higher id, " +
+                  std::to_string((unsigned long long)nnz - hup) + " to a lower one)");
         return fail(SCAN_EINVAL);
     }
     dev_free(c, badb);
