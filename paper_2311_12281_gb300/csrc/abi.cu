@@ -206,9 +206,9 @@ scan_status scan_ctx_stage_time(scan_ctx *c, int32_t stage, double *total_ms, in
 namespace scan {
 
 scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, bool on_dev,
-                         Graph **out) {
+                         Graph **out, const std::function<scan_status(Graph *)> &fill) {
     *out = nullptr;
-    if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj)) {
+    if (n < 0 || nnz < 0 || (!fill && ((n > 0 && !offsets) || (nnz > 0 && !adj)))) {
         set_error("bad sizes or NULL arrays");
         return SCAN_EINVAL;
     }
@@ -218,7 +218,7 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
         set_error("a resident graph needs nnz < 2^32 (use SCAN_LOAD_PINNED_BORROW)");
         return SCAN_EINVAL;
     }
-    if (!on_dev && n > 0) {  // cheap host-side check before any copy
+    if (!fill && !on_dev && n > 0) {  // cheap host-side check before any copy
         if (offsets[0] != 0 || offsets[n] != nnz) {
             set_error("offsets[0] must be 0 and offsets[n] must equal nnz");
             return SCAN_EINVAL;
@@ -249,10 +249,15 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
     cudaError_t e = cudaMallocHost(&g->h_npairs, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMallocHost(&g->h_err, sizeof(uint32_t));
     if (e != cudaSuccess) return fail(cuda_fail(e, "pinned staging"));
-    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    e = n > 0 ? cudaMemcpyAsync(g->off.ptr, offsets, 8 * N1, kind, ctx->stream)
-              : cudaMemsetAsync(g->off.ptr, 0, 8, ctx->stream);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(g->adj.ptr, adj, 4 * (size_t)nnz, kind, ctx->stream);
+    if (fill) {
+        const scan_status fs = fill(g);
+        if (fs != SCAN_OK) return fail(fs);
+    } else {
+        const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = n > 0 ? cudaMemcpyAsync(g->off.ptr, offsets, 8 * N1, kind, ctx->stream)
+                  : cudaMemsetAsync(g->off.ptr, 0, 8, ctx->stream);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(g->adj.ptr, adj, 4 * (size_t)nnz, kind, ctx->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(g->err.ptr, 0, 4, ctx->stream);
     // the flags are read 16 at a time: the padding after the last edge stays zero
     if (e == cudaSuccess) e = cudaMemsetAsync(g->simo.ptr, 0, g->simo.bytes, ctx->stream);

@@ -49,6 +49,31 @@ __global__ void k_graph_index(const int64_t *__restrict__ vbase, int32_t k, int3
     gid[v] = lo;
 }
 
+// Union assembly: each graph's rows were copied into place with local ids
+// and offsets; shift them by the graph's vertex and slot bases.
+__global__ void k_union_offsets(int64_t *__restrict__ off, int32_t n, const int32_t *__restrict__ gid,
+                                const int64_t *__restrict__ ebase) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) off[v] += ebase[gid[v]];
+}
+
+// per slot: its graph j (the last with ebase[j] <= s), the id range check
+// against that graph's n, and the shift by its vertex base
+__global__ void k_union_ids(int32_t *__restrict__ adj, int64_t nnz, const int64_t *__restrict__ vbase,
+                            const int64_t *__restrict__ ebase, int32_t k, unsigned long long *bad) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = k;  // ebase[lo] <= s < ebase[hi]
+        for (int it = 0; it < 40 && hi - lo > 1; ++it) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (ebase[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        const int32_t a = adj[s];
+        if (a < 0 || (int64_t)a >= vbase[lo + 1] - vbase[lo]) atomicMin(bad, (unsigned long long)s);
+        else adj[s] = a + (int32_t)vbase[lo];
+    }
+}
+
 void batch_release(scan_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -158,48 +183,75 @@ scan_status batch_create(Ctx *ctx, int32_t k, const int32_t *ns, const int64_t *
         set_error("the batch union exceeds 2^31 vertices or 2^32 slots");
         return fail(SCAN_EINVAL);
     }
-    // the union CSR: shifted offsets and ids
-    std::vector<int64_t> off((size_t)n + 1);
-    std::vector<int32_t> adj((size_t)std::max<int64_t>(nnz, 1));
-    for (int32_t j = 0; j < k; ++j) {
-        const int64_t vb = b->vbase[j], eb = b->ebase[j];
-        for (int32_t i = 0; i < ns[j]; ++i) off[(size_t)(vb + i)] = eb + offsets[j][i];
-        const int64_t m2 = b->ebase[j + 1] - eb;
-        const int32_t *a = adjs[j];
-        int32_t *dst = adj.data() + eb;
-        for (int64_t e = 0; e < m2; ++e) {
-            if (a[e] < 0 || a[e] >= ns[j]) {
-                set_error("graph " + std::to_string(j) + " of the batch: id out of range at slot " + std::to_string(e));
-                return fail(SCAN_EINVAL);
-            }
-            dst[e] = a[e] + (int32_t)vb;
-        }
-    }
-    off[(size_t)n] = nnz;
-    {
-        const scan_status gs = graph_create(ctx, (int32_t)n, off.data(), adj.data(), nnz, false, &b->g);
-        if (gs != SCAN_OK) return fail(gs);
-    }
-    // graph index of every vertex
-    DevBuf dvb;
+    // the union CSR, assembled on the device: every graph's arrays are copied
+    // into place as they are, then ids and offsets are shifted by the graph's
+    // bases (ids checked against the graph's own n there)
+    DevBuf dvb, deb, dbad;
     scan_status s = dev_alloc(ctx, dvb, 8 * ((size_t)k + 1));
+    if (s == SCAN_OK) s = dev_alloc(ctx, deb, 8 * ((size_t)k + 1));
+    if (s == SCAN_OK) s = dev_alloc(ctx, dbad, sizeof(unsigned long long));
     if (s == SCAN_OK) s = dev_alloc(ctx, b->gid, 4 * ((size_t)n + 1));
     if (s == SCAN_OK) s = dev_alloc(ctx, b->gpp, 8 * (size_t)k);
     if (s == SCAN_OK) s = dev_alloc(ctx, b->gqq, 8 * (size_t)k);
     if (s == SCAN_OK) s = dev_alloc(ctx, b->gmu, 4 * (size_t)k);
-    if (s != SCAN_OK) {
+    auto free_tmp = [&]() {
         dev_free(ctx, dvb);
+        dev_free(ctx, deb);
+        dev_free(ctx, dbad);
+    };
+    if (s != SCAN_OK) {
+        free_tmp();
         return fail(s);
     }
-    cudaError_t e = cudaMemcpyAsync(dvb.ptr, b->vbase.data(), 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess && n > 0) {
-        k_graph_index<<<grid_for(n, 256), 256, 0, ctx->stream>>>((const int64_t *)dvb.ptr, k, (int32_t)n,
-                                                                 (int32_t *)b->gid.ptr);
-        ctx->launches++;
+    auto fill = [&](Graph *g) -> scan_status {
+        cudaStream_t st = ctx->stream;
+        auto *doff = (int64_t *)g->off.ptr;
+        auto *dadj = (int32_t *)g->adj.ptr;
+        const unsigned long long none = ~0ull;
+        cudaError_t e = cudaMemcpyAsync(dvb.ptr, b->vbase.data(), 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(deb.ptr, b->ebase.data(), 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dbad.ptr, &none, sizeof(none), cudaMemcpyHostToDevice, st);
+        for (int32_t j = 0; j < k && e == cudaSuccess; ++j) {
+            const int64_t vb = b->vbase[j], eb = b->ebase[j], m2 = b->ebase[j + 1] - eb;
+            if (ns[j] > 0) e = cudaMemcpyAsync(doff + vb, offsets[j], 8 * (size_t)ns[j], cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && m2 > 0)
+                e = cudaMemcpyAsync(dadj + eb, adjs[j], 4 * (size_t)m2, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(doff + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+        if (n > 0) {
+            k_graph_index<<<grid_for(n, 256), 256, 0, st>>>((const int64_t *)dvb.ptr, k, (int32_t)n,
+                                                            (int32_t *)b->gid.ptr);
+            k_union_offsets<<<grid_for(n, 256), 256, 0, st>>>(doff, (int32_t)n, (const int32_t *)b->gid.ptr,
+                                                              (const int64_t *)deb.ptr);
+            ctx->launches += 2;
+        }
+        if (nnz > 0) {
+            k_union_ids<<<grid_for(nnz, 256, ctx->num_sms * 32), 256, 0, st>>>(
+                dadj, nnz, (const int64_t *)dvb.ptr, (const int64_t *)deb.ptr, k, (unsigned long long *)dbad.ptr);
+            ctx->launches++;
+        }
+        unsigned long long hbad = none;
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad.ptr, sizeof(hbad), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch union");
+        if (hbad != none) {
+            const int32_t j = (int32_t)(std::upper_bound(b->ebase.begin(), b->ebase.end(), (int64_t)hbad) -
+                                        b->ebase.begin()) - 1;
+            set_error("graph " + std::to_string(j) + " of the batch: id out of range at slot " +
+                      std::to_string((int64_t)hbad - b->ebase[(size_t)j]));
+            return SCAN_EINVAL;
+        }
+        return SCAN_OK;
+    };
+    {
+        const scan_status gs = graph_create(ctx, (int32_t)n, nullptr, nullptr, nnz, false, &b->g, fill);
+        free_tmp();
+        if (gs != SCAN_OK) return fail(gs);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    dev_free(ctx, dvb);
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_pp, 8 * (size_t)k);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_qq, 8 * (size_t)k);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_mu, 4 * (size_t)k);

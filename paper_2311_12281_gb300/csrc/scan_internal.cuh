@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -213,8 +214,11 @@ scan_status dev_alloc(Ctx *c, DevBuf &b, size_t bytes);
 void dev_free(Ctx *c, DevBuf &b);
 scan_status check_params(const scan_params *p);
 scan_status take_device_error(Graph *g);
+// Allocates and prepares a resident graph. The CSR comes from offsets/adj
+// (host, or device with on_dev), or -- when fill is given -- fill writes it
+// into g->off and g->adj on the context's stream (offsets/adj unused).
 scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, bool on_dev,
-                         Graph **out);
+                         Graph **out, const std::function<scan_status(Graph *)> &fill = nullptr);
 void graph_destroy(Graph *g);
 scan_result *result_new(int32_t n, int64_t k, bool pinned);
 bool result_set_pairs(scan_result *r, int64_t k);  // room for k pairs (r->k = k); false if out of memory
