@@ -238,6 +238,31 @@ def test_hub_test_directions_on_power_law_graphs(ps, ctx):
     assert seen == {True, False}
 
 
+def test_counting_tables_fall_back_when_cuckoo_insertion_fails(ps, ctx):
+    # White-box: 20905, 69480 and 93346 share both cuckoo slots of a 512-slot
+    # table under the counting kernel's two hash functions, so a table holding
+    # all three cannot place them and the CTA falls back to linear probing.
+    # Vertex 0 gets 100 higher-ranked neighbours including the three (its
+    # table: 100 keys, 512 slots), and so do the 131 filler vertices. Twenty
+    # low-degree vertices stream suffixes through vertex 0's table and close
+    # triangles with it. If the hashing changes, this still checks parity on
+    # the same graph, only not that path.
+    triple = [20905, 69480, 93346]
+    xs = triple + list(range(1000, 1097))
+    fillers = list(range(3000, 3131))
+    ins = list(range(2000, 2020))
+    edges = [(0, x) for x in xs] + [(x, f) for x in xs for f in fillers]
+    edges += [(0, v) for v in ins]
+    for i, v in enumerate(ins):
+        edges += [(v, triple[i % 3]), (v, triple[(i + 1) % 3]), (v, xs[3 + i])]
+    edges += [(triple[0], triple[1]), (triple[1], triple[2]), (triple[0], xs[3])]
+    g = gg.from_edges(100_000, edges)
+    g.name = "cuckoo fallback"
+    deg = g.degrees()
+    assert all(deg[x] > deg[0] for x in xs) and all(deg[v] < deg[0] for v in ins)
+    check_graph(ps, ctx, g, [(1, 5, 2), (1, 10, 3), (1, 2, 2), (3, 10, 5)], invariants=False)
+
+
 def test_query_entry_points_agree(ps, ctx):
     g = gg.rmat(12, 16, seed=9)
     dg = ctx.load(g)
