@@ -852,26 +852,29 @@ __global__ void k_fwd_sort_warp(const int64_t *__restrict__ foff, int32_t n, con
     }
 }
 
-// CTA per vertex with 32 < out-degree <= kSortMax: bitonic sort in shared memory
-__global__ void __launch_bounds__(1024) k_fwd_sort_cta(const int32_t *__restrict__ verts,
-                                                       const int64_t *__restrict__ foff,
-                                                       const int32_t *__restrict__ deg, int32_t *__restrict__ fadj,
-                                                       uint32_t *__restrict__ oe) {
-    __shared__ unsigned long long key[kSortMax];
-    __shared__ uint32_t pay[kSortMax];
+// CTA per vertex with an out-list of up to CAP (> 32) ids: bitonic sort in
+// shared memory. Three sizes (CAP 256, 1024, kSortMax on 128, 256 and 1024
+// threads), so short lists do not hold a 1024-thread CTA at its barriers.
+template <int BLOCK, int CAP>
+__global__ void __launch_bounds__(BLOCK) k_fwd_sort_cta(const int32_t *__restrict__ verts,
+                                                        const int64_t *__restrict__ foff,
+                                                        const int32_t *__restrict__ deg, int32_t *__restrict__ fadj,
+                                                        uint32_t *__restrict__ oe) {
+    __shared__ unsigned long long key[CAP];
+    __shared__ uint32_t pay[CAP];
     const int32_t a = verts[blockIdx.x];
     const int64_t b = foff[a];
     const int32_t len = (int32_t)(foff[a + 1] - b);
     int size = 64;
     while (size < len) size <<= 1;
-    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+    for (int i = threadIdx.x; i < size; i += BLOCK) {
         key[i] = i < len ? rank_key(deg, fadj[b + i]) : ~0ull;
         pay[i] = i < len ? oe[b + i] : 0u;
     }
     __syncthreads();
     for (int k = 2; k <= size; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < size; i += blockDim.x) {
+            for (int i = threadIdx.x; i < size; i += BLOCK) {
                 const int p = i ^ j;
                 if (p > i) {
                     const bool up = (i & k) == 0;
@@ -887,7 +890,7 @@ __global__ void __launch_bounds__(1024) k_fwd_sort_cta(const int32_t *__restrict
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    for (int i = threadIdx.x; i < len; i += BLOCK) {
         fadj[b + i] = (int32_t)(uint32_t)key[i];
         oe[b + i] = pay[i];
     }
@@ -900,13 +903,17 @@ __global__ void k_fwd_fin(const uint32_t *__restrict__ oe, int64_t m, const uint
 }
 
 // vertices whose out-list needs the CTA sort; flags a list too long to sort
-__global__ void k_fwd_sort_pick(const int64_t *__restrict__ foff, int32_t n, int32_t *__restrict__ verts,
-                                unsigned long long *counts) {
+// out-lists above a warp, by sort size: up to 256 (v256), 1024 (v1024) and
+// kSortMax (vmax); counts[3] = lists above kSortMax
+__global__ void k_fwd_sort_pick(const int64_t *__restrict__ foff, int32_t n, int32_t *__restrict__ v256,
+                                int32_t *__restrict__ v1024, int32_t *__restrict__ vmax, unsigned long long *counts) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     const int64_t len = foff[a + 1] - foff[a];
-    if (len > kSortMax) atomicAdd(counts + 1, 1ull);
-    else if (len > kWarp) verts[atomicAdd(counts + 0, 1ull)] = (int32_t)a;
+    if (len > kSortMax) atomicAdd(counts + 3, 1ull);
+    else if (len > 1024) vmax[atomicAdd(counts + 2, 1ull)] = (int32_t)a;
+    else if (len > 256) v1024[atomicAdd(counts + 1, 1ull)] = (int32_t)a;
+    else if (len > kWarp) v256[atomicAdd(counts + 0, 1ull)] = (int32_t)a;
 }
 
 __global__ void k_fwd_adj(const uint32_t *__restrict__ oe, int64_t m, const int32_t *__restrict__ adj,
@@ -1154,24 +1161,37 @@ scan_status fwd_prepare(Graph *g) {
         c->launches++;
         // order every out-list by rank, carrying the slot ids, then re-index fin
         SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
-        int32_t *verts = (int32_t *)g->cnt.ptr;  // scratch int32[n+1]
-        k_fwd_sort_pick<<<grid_for(n, 256), 256, 0, c->stream>>>((const int64_t *)g->foff.ptr, n, verts, counts);
-        unsigned long long h2[2];
-        SCAN_CUDA(cudaMemcpyAsync(h2, counts, sizeof(h2), cudaMemcpyDeviceToHost, c->stream));
+        // scratch int32[n+1] lists (free until the query's later stages)
+        int32_t *v256 = (int32_t *)g->cnt.ptr, *v1024 = (int32_t *)g->ucnt.ptr, *vmax = (int32_t *)g->parent.ptr;
+        k_fwd_sort_pick<<<grid_for(n, 256), 256, 0, c->stream>>>((const int64_t *)g->foff.ptr, n, v256, v1024, vmax,
+                                                                 counts);
+        unsigned long long h4[4];
+        SCAN_CUDA(cudaMemcpyAsync(h4, counts, sizeof(h4), cudaMemcpyDeviceToHost, c->stream));
         SCAN_CUDA(cudaStreamSynchronize(c->stream));
         c->launches++;
-        g->fwd_rank_sorted = h2[1] == 0;
+        g->fwd_rank_sorted = h4[3] == 0;
         if (g->fwd_rank_sorted) {
-            k_fwd_sort_warp<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(
-                (const int64_t *)g->foff.ptr, n, (const int32_t *)g->deg.ptr, (int32_t *)g->fadj.ptr,
-                (uint32_t *)g->oe.ptr);
-            if (h2[0] > 0)
-                k_fwd_sort_cta<<<(unsigned)h2[0], 1024, 0, c->stream>>>(verts, (const int64_t *)g->foff.ptr,
-                                                                       (const int32_t *)g->deg.ptr,
-                                                                       (int32_t *)g->fadj.ptr, (uint32_t *)g->oe.ptr);
+            auto *foff = (const int64_t *)g->foff.ptr;
+            auto *deg = (const int32_t *)g->deg.ptr;
+            auto *fadj = (int32_t *)g->fadj.ptr;
+            auto *oe = (uint32_t *)g->oe.ptr;
+            k_fwd_sort_warp<<<grid_for((int64_t)n * kWarp, 256), 256, 0, c->stream>>>(foff, n, deg, fadj, oe);
+            c->launches++;
+            if (h4[0] > 0) {
+                k_fwd_sort_cta<128, 256><<<(unsigned)h4[0], 128, 0, c->stream>>>(v256, foff, deg, fadj, oe);
+                c->launches++;
+            }
+            if (h4[1] > 0) {
+                k_fwd_sort_cta<256, 1024><<<(unsigned)h4[1], 256, 0, c->stream>>>(v1024, foff, deg, fadj, oe);
+                c->launches++;
+            }
+            if (h4[2] > 0) {
+                k_fwd_sort_cta<1024, kSortMax><<<(unsigned)h4[2], 1024, 0, c->stream>>>(vmax, foff, deg, fadj, oe);
+                c->launches++;
+            }
             k_fwd_fin<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
                 (const uint32_t *)g->oe.ptr, m, (const uint32_t *)g->rev.ptr, (uint32_t *)g->fin.ptr);
-            c->launches += 2 + (h2[0] > 0);
+            c->launches++;
         }
         k_fwd_src<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
             (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->src.ptr, (int32_t *)g->fsrc.ptr);
