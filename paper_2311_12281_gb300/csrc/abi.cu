@@ -238,7 +238,7 @@ scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int3
     const size_t N1 = (size_t)n + 1, E = (size_t)(nnz > 0 ? nnz : 1), M = (size_t)(g->m > 0 ? g->m : 1);
     struct { DevBuf *b; size_t bytes; } plan[] = {
         {&g->off, 8 * N1}, {&g->adj, 4 * E}, {&g->src, 4 * E}, {&g->rev, 4 * E}, {&g->deg, 4 * N1},
-        {&g->oe, 4 * M}, {&g->sim, E}, {&g->simo, (M + 15) & ~(size_t)15}, {&g->nsim, 4 * N1}, {&g->hst, 4 * N1},
+        {&g->oe, 4 * M}, {&g->simo, (M + 15) & ~(size_t)15}, {&g->nsim, 4 * N1}, {&g->hst, 4 * N1},
         {&g->mslots, 8}, {&g->core, N1}, {&g->cid, 4 * N1}, {&g->parent, 4 * N1},
         {&g->label, N1}, {&g->cnt, 4 * N1}, {&g->cnt_off, 8 * N1}, {&g->ucnt, 4 * N1}, {&g->pair_off, 8 * N1},
         {&g->raw, 4 * E}, {&g->pairs, 8 * E}, {&g->npairs, 8}, {&g->err, 4}};

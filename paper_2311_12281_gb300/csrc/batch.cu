@@ -9,6 +9,8 @@
 // union is the work queue over (graph, owner, slot range) items. Results are
 // split per graph on the host, with ids shifted back.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "scan_internal.cuh"
@@ -333,30 +335,53 @@ scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t 
         if (kp > 0)
             SCAN_CUDA(cudaMemcpyAsync(b->h_pairs, g->pairs.ptr, 8 * (size_t)kp, cudaMemcpyDeviceToHost, c->stream));
         SCAN_CUDA(cudaStreamSynchronize(c->stream));
-        // split: pairs are sorted by vertex, so each graph owns a contiguous run
-        int64_t pcur = 0;
-        for (int32_t j = 0; j < b->k; ++j) {
-            const int64_t vb = b->vbase[j], ve = b->vbase[j + 1];
-            int64_t pend = pcur;
-            while (pend < kp && b->h_pairs[2 * pend] < ve) ++pend;
-            scan_result *r = result_new((int32_t)(ve - vb), pend - pcur, false);
-            if (!r) {
-                for (int32_t i = 0; i < j; ++i) { scan_result_free(outs[i]); outs[i] = nullptr; }
-                set_error("result allocation failed");
-                return SCAN_ENOMEM;
+        // split: pairs are sorted by vertex, so each graph owns a contiguous
+        // run; the graphs are shared out over a few host threads
+        const int32_t k = b->k;
+        std::vector<int64_t> pstart((size_t)k + 1);
+        for (int32_t j = 0; j <= k; ++j) {
+            const int64_t vb = j < k ? b->vbase[j] : n;
+            int64_t lo = 0, hi = kp;  // first pair whose vertex is >= vb
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (b->h_pairs[2 * mid] < vb) lo = mid + 1;
+                else hi = mid;
             }
-            for (int64_t v = vb; v < ve; ++v) {
-                r->core[v - vb] = b->h_core[v];
-                r->label[v - vb] = b->h_label[v];
-                const int32_t x = b->h_cid[v];
-                r->cid[v - vb] = x >= 0 ? x - (int32_t)vb : -1;
+            pstart[(size_t)j] = lo;
+        }
+        std::atomic<bool> oom{false};
+        auto split = [&](int32_t j0, int32_t j1) {
+            for (int32_t j = j0; j < j1 && !oom.load(std::memory_order_relaxed); ++j) {
+                const int64_t vb = b->vbase[j], ve = b->vbase[j + 1];
+                const int64_t p0 = pstart[(size_t)j], p1 = pstart[(size_t)j + 1];
+                scan_result *r = result_new((int32_t)(ve - vb), p1 - p0, false);
+                if (!r) {
+                    oom = true;
+                    return;
+                }
+                for (int64_t v = vb; v < ve; ++v) {
+                    r->core[v - vb] = b->h_core[v];
+                    r->label[v - vb] = b->h_label[v];
+                    const int32_t x = b->h_cid[v];
+                    r->cid[v - vb] = x >= 0 ? x - (int32_t)vb : -1;
+                }
+                for (int64_t i = p0; i < p1; ++i) {
+                    r->pairs[2 * (i - p0)] = b->h_pairs[2 * i] - (int32_t)vb;
+                    r->pairs[2 * (i - p0) + 1] = b->h_pairs[2 * i + 1] - (int32_t)vb;
+                }
+                outs[j] = r;
             }
-            for (int64_t i = pcur; i < pend; ++i) {
-                r->pairs[2 * (i - pcur)] = b->h_pairs[2 * i] - (int32_t)vb;
-                r->pairs[2 * (i - pcur) + 1] = b->h_pairs[2 * i + 1] - (int32_t)vb;
-            }
-            outs[j] = r;
-            pcur = pend;
+        };
+        const int32_t nt = (int32_t)std::min<int64_t>({8, std::max(1u, std::thread::hardware_concurrency()), k});
+        std::vector<std::thread> pool;
+        for (int32_t t = 1; t < nt; ++t) pool.emplace_back(split, (int32_t)((int64_t)k * t / nt),
+                                                           (int32_t)((int64_t)k * (t + 1) / nt));
+        split(0, (int32_t)((int64_t)k / nt));
+        for (auto &th : pool) th.join();
+        if (oom) {
+            for (int32_t j = 0; j < k; ++j) { scan_result_free(outs[j]); outs[j] = nullptr; }
+            set_error("result allocation failed");
+            return SCAN_ENOMEM;
         }
         return SCAN_OK;
     } catch (...) {

@@ -673,7 +673,6 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     auto *src = (const int32_t *)g->src.ptr;
     auto *deg = (const int32_t *)g->deg.ptr;
     auto *oe = (const uint32_t *)g->oe.ptr;
-    auto *sim = (uint8_t *)g->sim.ptr;
     auto *simo = (uint8_t *)g->simo.ptr;
     auto *nsim = (int32_t *)g->nsim.ptr;
     auto *err = (uint32_t *)g->err.ptr;
@@ -695,7 +694,9 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
                    g->strategy != SCAN_STRATEGY_BSEARCH) {
             SCAN_TRY(launch_fwd_counts(g, true, false, qp, nullptr));  // k_fwd_finish writes simo, nsim
         } else {
-            // the per-edge families write per-slot flags
+            // the per-edge families write per-slot flags (allocated on their first use)
+            if (!g->sim.ptr) SCAN_TRY(dev_alloc(c, g->sim, (size_t)(nnz > 0 ? nnz : 1)));
+            uint8_t *sim = (uint8_t *)g->sim.ptr;
             if (nnz > 0) SCAN_CUDA(cudaMemsetAsync(sim, 0, (size_t)nnz, st));
             if (mode & SCAN_Q_PLAIN) SCAN_TRY(launch_isect(g, false, true, false, qp, nullptr));
             else if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, true, true, false, qp, nullptr));

@@ -90,7 +90,7 @@ struct Graph {
     bool heavy_ready = false;
     Part *part = nullptr;   // non-null: the CSR stays in host memory and is streamed in blocks
     // per-query scratch
-    DevBuf sim;             // uint8[nnz] 1 = eps-similar (per-slot output of the per-edge families)
+    DevBuf sim;             // uint8[nnz] 1 = eps-similar (per-slot output of the per-edge families; on first use)
     DevBuf simo;            // uint8[m] 1 = oriented edge oe[i] is eps-similar
     DevBuf nsim;            // int32[n+1] open eps-degree
     DevBuf hst;             // int32[n+1] hub test state of the label stage's push direction
