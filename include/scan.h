@@ -156,6 +156,8 @@ SCAN_API int32_t scan_graph_has_cache(const scan_graph *g);
 /* Copy the cached closed common counts |N[u] cap N[v]| (the numerator of
  * Definition 2.2's sigma, Eq. 1) to host memory out[nnz], slot-aligned with
  * adj. Requires a cache (a query with SCAN_Q_BUILD_CACHE), else SCAN_EINVAL.
+ * The cache keeps 12 bytes per undirected edge (the count and the product of
+ * the closed degrees); this call writes both slots of every edge.
  * Synchronous. */
 SCAN_API scan_status scan_graph_copy_counts(scan_graph *g, int32_t *out);
 

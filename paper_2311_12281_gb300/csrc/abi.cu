@@ -279,10 +279,11 @@ void graph_destroy(Graph *g) {
     delete static_cast<scan_graph *>(g);
 }
 
-// Pinned host blocks for query results, reused from one result to the next:
-// page-locking and unlocking memory costs far more than the copies into it.
-// Blocks are sized in powers of two; up to kPoolCap bytes of free blocks are
-// kept (the rest is released); the pool lives until the process exits.
+// Pinned host blocks for query results and staging, reused from one use to
+// the next: page-locking and unlocking memory costs far more than the copies
+// into it. Blocks are sized in powers of two; up to kPoolCap bytes of free
+// blocks are kept (the rest is released); the pool lives until the process
+// exits.
 namespace {
 std::mutex g_pool_mu;
 std::multimap<size_t, void *> g_pool;
@@ -294,6 +295,7 @@ size_t pool_size(size_t bytes) {
     while (s < bytes) s <<= 1;
     return s;
 }
+}  // namespace
 
 void *pinned_get(size_t bytes, size_t *cap) {
     const size_t sz = pool_size(bytes);
@@ -329,7 +331,6 @@ void pinned_put(void *p, size_t cap) {
     }
     cudaFreeHost(p);
 }
-}  // namespace
 
 scan_result *result_new(int32_t n, int64_t k, bool pinned) {
     scan_result *r = new scan_result();

@@ -9,6 +9,7 @@
 // union is the work queue over (graph, owner, slot range) items. Results are
 // split per graph on the host, with ids shifted back.
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 #include <thread>
 #include <vector>
@@ -29,6 +30,7 @@ struct scan_batch {
     uint8_t *h_core = nullptr, *h_label = nullptr;
     int32_t *h_cid = nullptr, *h_pairs = nullptr;
     int64_t h_pairs_cap = 0;
+    size_t cap[7] = {0, 0, 0, 0, 0, 0, 0};  // pinned pool block sizes of the seven staging arrays
     // the device query (parameter copies + pipeline), replayed as a CUDA graph
     cudaGraphExec_t exec = nullptr;
     uint64_t key = 0;
@@ -76,6 +78,64 @@ __global__ void k_union_ids(int32_t *__restrict__ adj, int64_t nnz, const int64_
     }
 }
 
+// Host-to-device upload of many pageable arrays that are contiguous on the
+// device: packed into pinned blocks by a few host threads (two blocks, so the
+// next is packed while the previous one is copied), one copy per block.
+struct Piece {
+    const char *src;
+    size_t bytes;
+};
+
+scan_status upload_concat(Ctx *ctx, const std::vector<Piece> &pieces, char *dst) {
+    constexpr size_t kBlock = size_t(128) << 20;
+    std::vector<size_t> start(pieces.size() + 1, 0);
+    for (size_t i = 0; i < pieces.size(); ++i) start[i + 1] = start[i] + pieces[i].bytes;
+    const size_t total = start.back();
+    if (total == 0) return SCAN_OK;
+    char *buf[2] = {nullptr, nullptr};
+    size_t cap[2] = {0, 0};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    scan_status st = SCAN_OK;
+    for (int i = 0; i < 2 && st == SCAN_OK; ++i) {
+        buf[i] = (char *)pinned_get(std::min(kBlock, total), &cap[i]);
+        if (!buf[i]) st = SCAN_ENOMEM;
+        else if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) st = SCAN_ENOMEM;
+    }
+    const int nt = (int)std::min<unsigned>(8, std::max(1u, std::thread::hardware_concurrency()));
+    // copies [a, b) of the concatenation into out
+    auto pack = [&](size_t a, size_t b, char *out) {
+        size_t i = (size_t)(std::upper_bound(start.begin(), start.end(), a) - start.begin()) - 1;
+        for (size_t pos = a; pos < b; ++i) {
+            const size_t lo = pos - start[i], n = std::min(start[i + 1], b) - pos;
+            if (n) memcpy(out + (pos - a), pieces[i].src + lo, n);
+            pos += n;
+        }
+    };
+    int cur = 0;
+    for (size_t off = 0; off < total && st == SCAN_OK; off += kBlock, cur ^= 1) {
+        const size_t len = std::min(kBlock, total - off);
+        if (cudaEventSynchronize(ev[cur]) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "batch upload"); break; }
+        std::vector<std::thread> pool;
+        const size_t share = (len + nt - 1) / nt;
+        for (int t = 1; t < nt; ++t) {
+            const size_t a = std::min(len, share * t), b2 = std::min(len, share * (t + 1));
+            if (a < b2) pool.emplace_back(pack, off + a, off + b2, buf[cur] + a);
+        }
+        pack(off, off + std::min(len, share), buf[cur]);
+        for (auto &th : pool) th.join();
+        cudaError_t e = cudaMemcpyAsync(dst + off, buf[cur], len, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[cur], ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch upload");
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (ev[i]) cudaEventDestroy(ev[i]);
+        pinned_put(buf[i], cap[i]);
+    }
+    if (st == SCAN_ENOMEM) set_error("pinned staging allocation failed");
+    return st;
+}
+
 void batch_release(scan_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -84,8 +144,7 @@ void batch_release(scan_batch *b) {
     DevBuf *bufs[] = {&b->gid, &b->gpp, &b->gqq, &b->gmu};
     for (DevBuf *d : bufs) dev_free(b->ctx, *d);
     void *pin[] = {b->h_pp, b->h_qq, b->h_mu, b->h_core, b->h_label, b->h_cid, b->h_pairs};
-    for (void *p : pin)
-        if (p) cudaFreeHost(p);
+    for (int i = 0; i < 7; ++i) pinned_put(pin[i], b->cap[i]);
     delete b;
 }
 
@@ -214,11 +273,18 @@ scan_status batch_create(Ctx *ctx, int32_t k, const int32_t *ns, const int64_t *
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(deb.ptr, b->ebase.data(), 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dbad.ptr, &none, sizeof(none), cudaMemcpyHostToDevice, st);
-        for (int32_t j = 0; j < k && e == cudaSuccess; ++j) {
-            const int64_t vb = b->vbase[j], eb = b->ebase[j], m2 = b->ebase[j + 1] - eb;
-            if (ns[j] > 0) e = cudaMemcpyAsync(doff + vb, offsets[j], 8 * (size_t)ns[j], cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess && m2 > 0)
-                e = cudaMemcpyAsync(dadj + eb, adjs[j], 4 * (size_t)m2, cudaMemcpyHostToDevice, st);
+        // the graphs' offset arrays (without their last entry) and adjacency
+        // arrays, concatenated, are exactly the union's before the shift
+        if (e == cudaSuccess) {
+            std::vector<Piece> offp, adjp;
+            for (int32_t j = 0; j < k; ++j) {
+                offp.push_back({(const char *)offsets[j], 8 * (size_t)ns[j]});
+                adjp.push_back({(const char *)adjs[j], 4 * (size_t)(b->ebase[j + 1] - b->ebase[j])});
+            }
+            const scan_status us = upload_concat(ctx, offp, (char *)doff);
+            if (us != SCAN_OK) return us;
+            const scan_status ua = upload_concat(ctx, adjp, (char *)dadj);
+            if (ua != SCAN_OK) return ua;
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(doff + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch upload");
@@ -253,14 +319,17 @@ scan_status batch_create(Ctx *ctx, int32_t k, const int32_t *ns, const int64_t *
         free_tmp();
         if (gs != SCAN_OK) return fail(gs);
     }
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_pp, 8 * (size_t)k);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_qq, 8 * (size_t)k);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_mu, 4 * (size_t)k);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_core, (size_t)n + 1);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_label, (size_t)n + 1);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_cid, 4 * ((size_t)n + 1));
-    if (e != cudaSuccess) return fail(cuda_fail(e, "batch setup"));
+    // parameter and result staging from the pinned pool (reused by the next batch)
+    b->h_pp = (uint64_t *)pinned_get(8 * (size_t)k, &b->cap[0]);
+    b->h_qq = (uint64_t *)pinned_get(8 * (size_t)k, &b->cap[1]);
+    b->h_mu = (uint32_t *)pinned_get(4 * (size_t)k, &b->cap[2]);
+    b->h_core = (uint8_t *)pinned_get((size_t)n + 1, &b->cap[3]);
+    b->h_label = (uint8_t *)pinned_get((size_t)n + 1, &b->cap[4]);
+    b->h_cid = (int32_t *)pinned_get(4 * ((size_t)n + 1), &b->cap[5]);
+    if (!b->h_pp || !b->h_qq || !b->h_mu || !b->h_core || !b->h_label || !b->h_cid) {
+        set_error("pinned staging allocation failed");
+        return fail(SCAN_ENOMEM);
+    }
     *out = b;
     return SCAN_OK;
 }
@@ -321,10 +390,13 @@ scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t 
         SCAN_TRY(take_device_error(g));
         const int64_t kp = *g->h_npairs, n = g->n;
         if (kp > b->h_pairs_cap) {
-            if (b->h_pairs) cudaFreeHost(b->h_pairs);
-            b->h_pairs = nullptr;
+            pinned_put(b->h_pairs, b->cap[6]);
             b->h_pairs_cap = 0;
-            SCAN_CUDA(cudaMallocHost(&b->h_pairs, 8 * (size_t)kp + 8));
+            b->h_pairs = (int32_t *)pinned_get(8 * (size_t)kp + 8, &b->cap[6]);
+            if (!b->h_pairs) {
+                set_error("pinned staging allocation failed");
+                return SCAN_ENOMEM;
+            }
             b->h_pairs_cap = kp;
         }
         if (n > 0) {

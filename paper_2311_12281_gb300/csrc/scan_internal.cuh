@@ -220,6 +220,9 @@ scan_status take_device_error(Graph *g);
 scan_status graph_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, bool on_dev,
                          Graph **out, const std::function<scan_status(Graph *)> &fill = nullptr);
 void graph_destroy(Graph *g);
+// pinned host blocks from a pool: at least `bytes` (block size in *cap), null if out of memory
+void *pinned_get(size_t bytes, size_t *cap);
+void pinned_put(void *p, size_t cap);  // back to the pool (p may be null)
 scan_result *result_new(int32_t n, int64_t k, bool pinned);
 bool result_set_pairs(scan_result *r, int64_t k);  // room for k pairs (r->k = k); false if out of memory
 // out of core (partition.cu)
