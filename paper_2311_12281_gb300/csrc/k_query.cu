@@ -146,10 +146,21 @@ __global__ void __launch_bounds__(kBlock) k_sim_orient(const int32_t *__restrict
 }
 
 // ------------------------------------------------------------------ cores
-// |N_eps[u]| = 1 + nsim[u] (u is eps-similar to itself)
-__global__ void k_core(const int32_t *__restrict__ nsim, int32_t n, QParams qp, uint8_t *__restrict__ core) {
+// |N_eps[u]| = 1 + nsim[u] (u is eps-similar to itself). The same pass
+// starts the later stages' per-vertex state: the union-find parent (cores
+// are their own roots), the border candidate count, the hub-test state and
+// the clustered-slot sum, so no separate clearing launches are needed.
+__global__ void k_core(const int32_t *__restrict__ nsim, int32_t n, QParams qp, uint8_t *__restrict__ core,
+                       int32_t *__restrict__ parent, int32_t *__restrict__ cnt, int32_t *__restrict__ hst,
+                       unsigned long long *__restrict__ member_slots) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u < n) core[u] = (uint32_t)nsim[u] + 1u >= qp.mu_of((int32_t)u) ? 1 : 0;
+    if (u == 0) *member_slots = 0;
+    if (u >= n) return;
+    const bool c = (uint32_t)nsim[u] + 1u >= qp.mu_of((int32_t)u);
+    core[u] = c ? 1 : 0;
+    parent[u] = c ? (int32_t)u : -1;
+    cnt[u] = 0;
+    hst[u] = 0;
 }
 
 // ------------------------------------------------------------------ heavy rows
@@ -221,11 +232,6 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, 
         if (old == b) return;
     }
     atomicOr(err, ERR_UF_LIMIT);
-}
-
-__global__ void k_uf_init(const uint8_t *__restrict__ core, int32_t n, int32_t *__restrict__ parent) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u < n) parent[u] = core[u] ? (int32_t)u : -1;
 }
 
 // core-core similar edges join clusters
@@ -717,30 +723,28 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     const int32_t nh = g->n_heavy;
     const int32_t *heavy = (const int32_t *)g->heavy.ptr;
     const unsigned gt = grid_for(n, kBlock);
+    int32_t *parent = (int32_t *)g->parent.ptr;
+    int32_t *cnt = (int32_t *)g->cnt.ptr;
+    int32_t *hst = (int32_t *)g->hst.ptr;
+    auto *mslots = (unsigned long long *)g->mslots.ptr;
     {
         StageTimer t(c, SCAN_STAGE_CORE);
-        k_core<<<gt, kBlock, 0, st>>>(nsim, n, qp, core);
+        k_core<<<gt, kBlock, 0, st>>>(nsim, n, qp, core, parent, cnt, hst, mslots);
         c->launches++;
     }
     {
         StageTimer t(c, SCAN_STAGE_CLUSTER);
-        int32_t *parent = (int32_t *)g->parent.ptr;
-        k_uf_init<<<gt, kBlock, 0, st>>>(core, n, parent);
         if (m > 0) k_uf_hook<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, parent, err);
         k_uf_final<<<gt, kBlock, 0, st>>>(core, n, parent, cid, err);
-        c->launches += 2 + (m > 0);
+        c->launches += 1 + (m > 0);
     }
-    int32_t *cnt = (int32_t *)g->cnt.ptr;
     int64_t *cnt_off = (int64_t *)g->cnt_off.ptr;
     int32_t *ucnt = (int32_t *)g->ucnt.ptr;
     int64_t *pair_off = (int64_t *)g->pair_off.ptr;
     int32_t *raw = (int32_t *)g->raw.ptr;
-    int32_t *memb = (int32_t *)g->parent.ptr;  // membership codes once union-find is done
-    auto *mslots = (unsigned long long *)g->mslots.ptr;
+    int32_t *memb = parent;  // membership codes once union-find is done
     {
         StageTimer t(c, SCAN_STAGE_BORDER);
-        SCAN_CUDA(cudaMemsetAsync(cnt, 0, 4 * (size_t)n, st));
-        SCAN_CUDA(cudaMemsetAsync(mslots, 0, sizeof(unsigned long long), st));
         if (m > 0) {
             k_border_count<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, cnt);
             c->launches++;
@@ -758,8 +762,6 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     }
     {
         StageTimer t(c, SCAN_STAGE_LABEL);
-        int32_t *hst = (int32_t *)g->hst.ptr;
-        SCAN_CUDA(cudaMemsetAsync(hst, 0, 4 * (size_t)n, st));
         k_label_push<<<gt, kBlock, 0, st>>>(off, adj, memb, n, nnz, mslots, hst);
         c->launches++;
         if (nh > 0) {
