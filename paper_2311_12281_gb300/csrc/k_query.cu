@@ -677,7 +677,6 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     auto *off = (const int64_t *)g->off.ptr;
     auto *adj = (const int32_t *)g->adj.ptr;
     auto *src = (const int32_t *)g->src.ptr;
-    auto *deg = (const int32_t *)g->deg.ptr;
     auto *oe = (const uint32_t *)g->oe.ptr;
     auto *simo = (uint8_t *)g->simo.ptr;
     auto *nsim = (int32_t *)g->nsim.ptr;
