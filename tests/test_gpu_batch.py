@@ -80,6 +80,38 @@ def test_query_batch_over_loaded_graphs(ps, ctx):
             ps.scan_graph_free(h)
 
 
+def test_batch_larger_than_one_upload_block(ps, ctx):
+    # 24 R-MAT graphs of about 1M edges: the union's adjacency (about 190 MB)
+    # goes up in several pinned blocks, some graphs straddling two of them.
+    # Each member must match the same graph queried alone (a path the oracle
+    # checks at smaller sizes) and its counts must match the oracle on samples.
+    graphs = [gg.rmat(16, 16, seed=600 + j) for j in range(24)]
+    assert sum(g.adj.nbytes for g in graphs) > (128 << 20)
+    params = [(1 + j % 4, 5, 2 + j % 5) for j in range(len(graphs))]
+    b = ps.scan_batch_load(ctx.handle, graphs)
+    try:
+        res = ps.scan_batch_query(b, params)
+        for j, (g, (p, q, mu), r) in enumerate(zip(graphs, params, res)):
+            dg = ctx.load(g)
+            try:
+                assert_same(r, dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE), f"member {j}")
+            finally:
+                dg.free()
+        # the union's counts, slot by slot, against the oracle on a sample
+        cache = ps.scan_batch_query(b, params, ps.SCAN_Q_BUILD_CACHE)
+        for r, want in zip(cache, res):
+            assert_same(r, want)
+        counts = ps.scan_graph_copy_counts(ps.scan_batch_union(b), sum(g.nnz for g in graphs))
+        base = 0
+        rng = np.random.default_rng(5)
+        for g in graphs[:3]:
+            slots = rng.integers(0, g.nnz, 2000)
+            assert np.array_equal(counts[base + slots], oracle.counts_for_slots(g, slots))
+            base += g.nnz
+    finally:
+        ps.scan_batch_free(b)
+
+
 def test_batch_rejects_bad_members(ps, ctx):
     bad = gg.from_csr([0, 1, 2, 2], [1, 2])  # asymmetric
     with pytest.raises(ps.ScanError) as ei:
