@@ -37,7 +37,11 @@ import graphgen as gg  # noqa: E402
 
 METRIC = "SCAN edges/s"
 UNIT = "edges/s"
-WORKLOAD = "rmat_s22_ef16_sweep21"
+
+
+def workload_name(scale: int) -> str:
+    """The sweep workload's name at an R-MAT scale (22: the benchmark workload)."""
+    return f"rmat_s{scale}_ef16_sweep21"
 
 
 def parse():
@@ -214,10 +218,10 @@ def run_reference(args):
             info = (k, el, thr)
     value = statistics.median(vals)
     sample = (f"oracle common-count step on {info[0]} uniformly sampled degree-oriented edges of the "
-              f"{WORKLOAD} graph per step ({info[1]:.1f} s); linear steps excluded")
+              f"{workload_name(args.scale)} graph per step ({info[1]:.1f} s); linear steps excluded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "i32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "m": g.m},
+            "data": "synthetic", "config": {"workload": workload_name(args.scale), "n": g.n, "m": g.m},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info[2], "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -659,7 +663,7 @@ def main():
             with open(os.path.join(_build.CSRC, f), "rb") as fh:
                 h.update(fh.read())
         # only while the kernels that were captured are unchanged
-        if (tr.get("kernel_hash") == h.hexdigest()[:16] and tr.get("workload") == WORKLOAD
+        if (tr.get("kernel_hash") == h.hexdigest()[:16] and tr.get("workload") == workload_name(args.scale)
                 and tr.get("mode") == args.mode and strategy == ps.SCAN_STRATEGY_FORWARD):
             traffic = tr.get("bytes_per_launch")
     except (OSError, ImportError, ValueError):
@@ -669,7 +673,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), seed 2",
+        "config": {"workload": workload_name(args.scale), "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), seed 2",
                    "n": g.n, "m": g.m, "queries_per_step": len(queries), "mode": args.mode,
                    "parallelism": "replicas" if world > 1 else "single",
                    "autotuned": {"strategy": tuned[0], "count_ms": tuned[1]} if tuned else None,
