@@ -114,15 +114,15 @@ def forward_bytes(g):
     streams the part of out(a) above b (sum over a of d+(d+-1)/2 ids), each
     owner's out-list once, the owner-row planning reads (id, degree, forward
     index: 12 B per slot), the per-edge counter cleared, updated once per
-    edge and read back (12 B per oriented edge), one similarity byte per slot
-    and the offsets. Triangle atomics are not counted."""
+    edge and read back (12 B per oriented edge), one similarity flag per
+    oriented edge and the offsets. Triangle atomics are not counted."""
     deg = g.degrees()
     src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
     dst = g.adj.astype(np.int64)
     fwd = (deg[dst] > deg[src]) | ((deg[dst] == deg[src]) & (dst > src))
     dplus = np.bincount(src[fwd], minlength=g.n).astype(np.float64)
     suffix = float((dplus * (dplus - 1) / 2).sum())
-    return 4.0 * suffix + 4.0 * g.m + 12.0 * g.nnz + 12.0 * g.m + 1.0 * g.nnz + 8.0 * (g.n + 1)
+    return 4.0 * suffix + 4.0 * g.m + 12.0 * g.nnz + 12.0 * g.m + 1.0 * g.m + 8.0 * (g.n + 1)
 
 
 # --------------------------------------------------------------- clocks
@@ -638,7 +638,7 @@ def main():
     if args.mode == "recompute" and strategy == ps.SCAN_STRATEGY_FORWARD:
         own_step = forward_bytes(g) * len(queries)
         own_def = ("triangle enumeration: streamed out-list suffixes (4 B/id) + owner lists + "
-                   "planning reads + counters + similarity bytes + offsets")
+                   "planning reads + counters + similarity flags + offsets")
     else:
         own_step, own_def = b_step, bytes_def
     if args.mode == "cache":
