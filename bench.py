@@ -39,6 +39,24 @@ METRIC = "SCAN edges/s"
 UNIT = "edges/s"
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The slowest rank's figure (every rank calls this; without a process
+    group, the figure itself). Timings of replicas are taken as the max."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed as the slowest rank's `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def workload_name(scale: int) -> str:
     """The sweep workload's name at an R-MAT scale (22: the benchmark workload)."""
     return f"rmat_s{scale}_ef16_sweep21"
@@ -614,13 +632,11 @@ def main():
     ps.scan_ctx_profile(ctx.handle, False)
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = max_over_ranks(elapsed_ms, dist)
         dist.barrier()
-        elapsed_ms = float(t.item())
     ms_per_step = elapsed_ms / args.steps
     edges_per_step = len(queries) * g.m
-    value = world * edges_per_step / (ms_per_step / 1e3)
+    value = replica_rate(edges_per_step, world, ms_per_step / 1e3)
 
     # roofline of the similarity stage (the dominant kernel), three ways:
     # SURVEY's per-edge algorithmic bytes B(eps) (what a pruned per-edge
@@ -729,10 +745,8 @@ def main():
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t) / ke
         if dist:
-            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        result["e2e"] = {"value": world * edges_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            e2e_s = max_over_ranks(e2e_s, dist)
+        result["e2e"] = {"value": replica_rate(edges_per_step, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h, "s_per_step": e2e_s}
 
     dg.free()
