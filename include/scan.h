@@ -216,6 +216,9 @@ SCAN_API const int32_t *scan_result_cluster(const scan_result *r);  /* [n] clust
 SCAN_API const uint8_t *scan_result_label(const scan_result *r);    /* [n] SCAN_CORE/BORDER/HUB/OUTLIER */
 SCAN_API int64_t scan_result_border_count(const scan_result *r);    /* k */
 SCAN_API const int32_t *scan_result_border_pairs(const scan_result *r); /* [2k] (v, c) ascending by (v, c) */
+/* Releases a result. Results of resident queries and of the server live in
+ * page-locked host blocks that the library pools (up to 2 GiB of free blocks
+ * are kept for reuse); freeing a result promptly returns its blocks. */
 SCAN_API void scan_result_free(scan_result *r);
 
 /*
