@@ -638,10 +638,10 @@ def main():
     edges_per_step = len(queries) * g.m
     value = replica_rate(edges_per_step, world, ms_per_step / 1e3)
 
-    # roofline of the similarity stage (the dominant kernel), three ways:
-    # SURVEY's per-edge algorithmic bytes B(eps) (what a pruned per-edge
-    # intersection must move for these queries), the kernel's own algorithmic
-    # bytes, and the DRAM traffic ncu measured per launch (profiles/traffic.json)
+    # roofline of the similarity stage (the dominant kernel), three ways: the
+    # per-edge algorithmic bytes B(eps) (what a pruned per-edge intersection
+    # must move for these queries), the kernel's own algorithmic bytes, and
+    # the DRAM traffic ncu measured per launch (profiles/traffic.json)
     sim_ms, sim_n = stage_ms["similarity"]
     strategy = ps.scan_graph_strategy(dg.handle)
     if args.mode == "plain":
