@@ -27,7 +27,10 @@
  *
  * Parity status: pinned (worked values of Example 3.1 and Example 4.2,
  * reconstructed Figure-1 fixture, closed forms, brute force over all graphs
- * with up to 7 vertices and sampled 8-12 vertex graphs).
+ * with up to 7 vertices and sampled 8-12 vertex graphs). The per-slot
+ * counts of oracle_counts_for_slots are pinned to the sparse matrix square
+ * (A^2)[u, v] + 2 on every slot of graphs with empty rows and with degree
+ * ratios above 32 (its binary-search branch).
  */
 #include <stdint.h>
 #include <stdlib.h>

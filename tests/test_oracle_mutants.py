@@ -29,6 +29,12 @@ MUTANTS = {
     "hub threshold off by one": ("label[u] = (uint8_t)(k >= 2 ? LABEL_HUB", "label[u] = (uint8_t)(k >= 1 ? LABEL_HUB"),
     "core threshold strict": ("core[u] = (uint8_t)(e_u >= (int64_t)mu);", "core[u] = (uint8_t)(e_u > (int64_t)mu);"),
     "mirror slot not written": ("cn[find_slot(off, adj, v, (int32_t)u)] = (int32_t)(c + 2);", ""),
+    "slot row search overshoots into the next row": ("if (off[mid] <= s) lo = mid; else hi = mid;",
+                                                      "if (off[mid] <= s + 1) lo = mid; else hi = mid;"),
+    "slot row search skips one row too many": ("while (lo + 1 <= n && off[lo + 1] <= s) ++lo;",
+                                               "while (lo + 1 <= n && off[lo + 1] <= s + 1) ++lo;"),
+    "slot count drops a shared endpoint": ("out[i] = (int32_t)(c + 2);", "out[i] = (int32_t)(c + 1);"),
+    "slot column taken from the row's first slot": ("int64_t u = lo, v = adj[s];", "int64_t u = lo, v = adj[off[lo]];"),
 }
 
 
@@ -41,6 +47,7 @@ def _compile(tmp_path, name, src_text):
     lib = ctypes.CDLL(str(so))
     vp, i64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int
     lib.oracle_common_counts.argtypes = [i64, vp, vp, vp, i32]
+    lib.oracle_counts_for_slots.argtypes = [i64, vp, vp, vp, i64, vp, i32]
     lib.oracle_scan.restype = i32
     lib.oracle_scan.argtypes = [i64, vp, vp, u32, u32, u32, i32, vp, vp, vp, vp, vp, vp]
     lib.brute_exhaustive.restype = i64
@@ -79,6 +86,18 @@ def _pins_pass(lib) -> bool:
     lib.oracle_common_counts(h.n, h.offsets.ctypes.data, h.adj.ctypes.data, cn.ctypes.data, 1)
     if not np.array_equal(cn, np.asarray((A @ A)[src, h.adj]).ravel() + 2):
         return False
+    # the per-slot checker on every slot: isolated vertices (empty rows) and a
+    # hub 60 times its partners' degree (binary search)
+    edges = [(0, k) for k in range(1, 121)] + [(k, k + 1) for k in range(1, 120, 2)] + [(130, 131)]
+    for sg in (gg.from_edges(135, edges), gg.chung_lu(400, 3.0, 2.1, seed=5)):
+        B = sp.csr_matrix((np.ones(sg.nnz, np.int64), sg.adj, sg.offsets), shape=(sg.n, sg.n))
+        want = np.asarray((B @ B).tocsr()[np.repeat(np.arange(sg.n), sg.degrees()), sg.adj]).ravel() + 2
+        slots = np.random.default_rng(1).permutation(sg.nnz).astype(np.int64)
+        out = np.zeros(sg.nnz, np.int32)
+        lib.oracle_counts_for_slots(sg.n, sg.offsets.ctypes.data, sg.adj.ctypes.data, slots.ctypes.data, sg.nnz,
+                                    out.ctypes.data, 1)
+        if not np.array_equal(out, want[slots]):
+            return False
     ds = gg.from_edges(6, [(0, 1), (0, 2), (0, 3), (1, 4), (1, 5)])
     if _scan(lib, ds, 1, 2, 3)[1][1] != 0:
         return False

@@ -78,6 +78,35 @@ def test_common_counts_equal_the_matrix_square():
         assert np.array_equal(oracle.common_counts(g, threads=3), want)
 
 
+def slot_pin_graphs():
+    """Graphs for the per-slot counts: isolated vertices between non-empty
+    rows (empty rows share their offset with the next row), and a hub whose
+    degree is more than 32 times its neighbours' (the binary-search branch),
+    with partner leaves so that those edges have common neighbours."""
+    hub_edges = [(0, k) for k in range(1, 121)] + [(k, k + 1) for k in range(1, 120, 2)]
+    sparse_edges = [(1, 5), (5, 9), (1, 9), (9, 14), (14, 20), (20, 5), (27, 28)]
+    return [gg.from_edges(126, hub_edges + [(123, 124)]), gg.from_edges(30, sparse_edges),
+            gg.chung_lu(500, 3.0, 2.1, seed=5), gg.rmat(9, 8, seed=3)]
+
+
+def test_counts_for_slots_equal_the_matrix_square():
+    # the sampled full-size checker: every slot, in a shuffled order, against
+    # (A^2)[u, v] + 2 from scipy's sparse product
+    rng = np.random.default_rng(0)
+    for g in slot_pin_graphs():
+        deg = g.degrees()
+        assert (deg == 0).any()
+        A = sp.csr_matrix((np.ones(g.nnz, dtype=np.int64), g.adj, g.offsets), shape=(g.n, g.n))
+        src = np.repeat(np.arange(g.n), deg)
+        want = np.asarray((A @ A).tocsr()[src, g.adj]).ravel() + 2
+        slots = rng.permutation(g.nnz)
+        assert np.array_equal(oracle.counts_for_slots(g, slots), want[slots])
+        assert np.array_equal(oracle.counts_for_slots(g, slots, threads=3), want[slots])
+    hub = slot_pin_graphs()[0]
+    d = hub.degrees()
+    assert d[0] == 120 and d[1] == 2 and d[0] // d[1] > 32  # the binary-search branch runs
+
+
 def test_eps_equality_boundary_is_inclusive():
     # double star u=0 - v=1 with two leaves each: sigma(u, v) = 2/sqrt(4*4) = 1/2 exactly
     edges = [(0, 1), (0, 2), (0, 3), (1, 4), (1, 5)]
