@@ -37,11 +37,13 @@ constexpr unsigned long long kSlotEmpty = ~0ull;
 
 // A CTA work item: owner v, value chunk of out(v), slot range [sb, se) of
 // v's row; with precomputed entry lists, the item's entries start at e0 (the
-// nlong long ones first, then the short ones).
+// nlong long ones first, then the short ones). hspan > 0: the owner's table
+// is a bitmap over the dense ids [hlo, hlo + hspan) (else a hash table).
 struct FItem {
     int32_t v, chunk, sb, se;
     int64_t e0;
     int32_t nlong, nent;
+    int32_t hlo, hspan;
 };
 
 __device__ __forceinline__ uint32_t fhash(int32_t x, int logc) { return ((uint32_t)x * 0x9E3779B1u) >> (32 - logc); }
@@ -529,15 +531,36 @@ __global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items
                                                        const int32_t *__restrict__ fadj,
                                                        const uint32_t *__restrict__ fin, int rank_sorted,
                                                        int32_t *__restrict__ e_base, int32_t *__restrict__ e_len,
-                                                       uint32_t *__restrict__ e_fin) {
+                                                       uint32_t *__restrict__ e_fin,
+                                                       const int32_t *__restrict__ fhid, int32_t cap_words,
+                                                       int cap_logs, int load_shift, int32_t *need_words) {
     __shared__ int32_t hist[kEntBuckets], boff[kEntBuckets];
+    __shared__ int32_t hmin, hmax;
     FItem it = items[blockIdx.x];
     const int32_t b = it.v;
     const int64_t rb = off[b], fb = foff[b];
     const int32_t db = (int32_t)(off[b + 1] - rb), ob = (int32_t)(foff[b + 1] - fb);
     const ItemBounds ib = item_bounds(it, deg, fadj, fb, ob);
     for (int k = threadIdx.x; k < kEntBuckets; k += 256) hist[k] = 0;
+    if (threadIdx.x == 0) {
+        hmin = INT32_MAX;
+        hmax = -1;
+    }
     __syncthreads();
+    // dense-id span of the item's part of out(b): its bitmap table's extent
+    const int32_t tb = it.chunk * kFwdChunk, tlen = min(tb + kFwdChunk, ob) - tb;
+    if (fhid != nullptr) {
+        int32_t lo = INT32_MAX, hi = -1, bad = 0;
+        for (int32_t k = threadIdx.x; k < tlen; k += 256) {
+            const int32_t h = fhid[fb + tb + k];
+            bad |= h < 0;
+            lo = min(lo, h);
+            hi = max(hi, h);
+        }
+        if (bad) hi = INT32_MAX;  // an element without a dense id: no bitmap
+        atomicMin(&hmin, lo);
+        atomicMax(&hmax, hi);
+    }
     for (int32_t rel = it.sb + threadIdx.x; rel < it.se; rel += 256) {
         int32_t base;
         uint32_t fab;
@@ -556,6 +579,20 @@ __global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items
         it.e0 = ebase_shift + eoff[blockIdx.x];
         it.nlong = nlong;
         it.nent = acc;
+        // 16 ids per 32-bit word (the high half holds the word's prefix
+        // count), then one count per element of the part of out(b)
+        it.hlo = 0;
+        it.hspan = 0;
+        int32_t words = 2 << min(cap_logs, max(5, fceil_log2(tlen << load_shift)));  // hash: keys and counts
+        if (fhid != nullptr && hmax >= hmin && hmax != INT32_MAX) {
+            const int64_t span = (int64_t)hmax - hmin + 1;
+            if ((span + 15) / 16 + tlen <= (int64_t)cap_words) {
+                it.hlo = hmin;
+                it.hspan = (int32_t)span;
+                words = (int32_t)((span + 15) / 16 + tlen);
+            }
+        }
+        atomicMax(need_words, words);
         items[blockIdx.x] = it;
     }
     __syncthreads();
@@ -643,64 +680,112 @@ __device__ __forceinline__ int32_t tab_find(const FTable &t, int32_t key) {
     return LP ? lp_find(t, key) : ck_find(t, key);
 }
 
+// Hash table of an owner, as the streaming loop sees it: count slot of an id.
+template <bool LP>
+struct HashTab {
+    FTable t;
+    __device__ __forceinline__ int32_t find(int32_t x) const { return tab_find<LP>(t, x); }
+    __device__ __forceinline__ int *counts() const { return t.cnt; }
+};
+
+// Bitmap table over dense ids. Every vertex has a dense id, given in order of
+// degree level (floor(log2 deg)), highest level first, then by id; an owner b
+// and every element it meets (its out-neighbours, and the streamed suffix
+// elements, all ranked above b) have degree >= deg(b), so the ids an owner
+// meets stay below the count of vertices of its level and above. Each 32-bit
+// word holds 16 ids in its low half and, in its high half, the number of
+// the owner's elements in the words below it, so one load answers a probe:
+// a set bit, and the element's count slot = prefix + set bits below it.
+struct BitTab {
+    uint32_t *w;
+    int *cnt;
+    int32_t lo;
+    uint32_t span;
+    __device__ __forceinline__ int32_t find(int32_t x) const {
+        const uint32_t r = (uint32_t)(x - lo);  // -2 padding and ids below lo wrap above span
+        if (r >= span) return -1;
+        const uint32_t y = w[r >> 4], s = r & 15u;
+        return ((y >> s) & 1u) ? (int32_t)((y >> 16) + __popc(y & ((1u << s) - 1u))) : -1;
+    }
+    __device__ __forceinline__ int *counts() const { return cnt; }
+};
+
 constexpr int kEntUnroll = 4;
+constexpr int kEntBatch = 8;  // long entries a warp takes at a time
 
 // Streams the item's entries: long ones one per warp (taken in turn, lanes on
 // consecutive ids), then short ones 32 at a time, one per lane (neighbours in
 // the sorted order have about the same length, so the lanes stay busy).
-// Positions past an entry's end read as -2, which no lookup finds.
-template <bool LP>
-__device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
-                                           const int32_t *__restrict__ fadj, const int32_t *__restrict__ e_base,
-                                           const int32_t *__restrict__ e_len, const uint32_t *__restrict__ e_fin,
-                                           int32_t *__restrict__ fcnt, int32_t *next_long, int32_t *next_short) {
+// Positions past an entry's end read as -2, which no lookup finds. `xs` is
+// what the table is keyed by, position for position with fadj: the vertex
+// ids for a hash table, the dense ids for a bitmap.
+template <class TAB>
+__device__ __forceinline__ void ent_stream(const FItem &it, const TAB &t, const int32_t *__restrict__ xs,
+                                           const int32_t *__restrict__ e_base, const int32_t *__restrict__ e_len,
+                                           const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
+                                           int32_t *next_long, int32_t *next_short) {
     const int lane = threadIdx.x & 31;
+    int *tc = t.counts();
     const int32_t nlong = it.nlong, nshort = it.nent - it.nlong;
-    for (int32_t guard = 0; guard <= nlong; ++guard) {
-        int32_t k = 0;
-        if (lane == 0) k = atomicAdd(next_long, 1);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= nlong) break;
-        const int64_t e = it.e0 + k;
-        const int32_t eb = e_base[e], el = e_len[e];
-        int c = 0;
-        // whole groups of kEntUnroll * 32 ids: every lane busy, no bounds checks
-        int32_t j0 = 0;
-        for (; j0 + kWarp * kEntUnroll <= el; j0 += kWarp * kEntUnroll) {
-            int32_t x[kEntUnroll];
+    // Long entries, kEntBatch at a time per warp: lane l holds the descriptor
+    // of the batch's entry l (one load per array for the whole batch), and
+    // the warp streams the batch's entries one after the other.
+    for (int32_t guard = 0; guard <= nlong; guard += kEntBatch) {
+        int32_t k0 = 0;
+        if (lane == 0) k0 = atomicAdd(next_long, kEntBatch);
+        k0 = __shfl_sync(0xffffffffu, k0, 0);
+        if (k0 >= nlong) break;
+        const int nb = min(kEntBatch, nlong - k0);
+        int32_t deb = 0, del = 0;
+        uint32_t def = 0;
+        if (lane < nb) {
+            const int64_t e = it.e0 + k0 + lane;
+            deb = e_base[e];
+            del = e_len[e];
+            def = e_fin[e];
+        }
+        for (int i = 0; i < nb; ++i) {
+            const int32_t eb = __shfl_sync(0xffffffffu, deb, i), el = __shfl_sync(0xffffffffu, del, i);
+            int c = 0;
+            // whole groups of kEntUnroll * 32 ids: every lane busy, no bounds checks
+            int32_t j0 = 0;
+            for (; j0 + kWarp * kEntUnroll <= el; j0 += kWarp * kEntUnroll) {
+                int32_t x[kEntUnroll];
 #pragma unroll
-            for (int u = 0; u < kEntUnroll; ++u) x[u] = __ldg(fadj + eb + j0 + u * kWarp + lane);
+                for (int u = 0; u < kEntUnroll; ++u) x[u] = __ldg(xs + eb + j0 + u * kWarp + lane);
 #pragma unroll
-            for (int u = 0; u < kEntUnroll; ++u) {
-                const int32_t r = tab_find<LP>(t, x[u]);
-                if (r >= 0) {
-                    ++c;
-                    atomicAdd(t.cnt + r, 1);                             // edge (b, c)
-                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);  // edge (a, c)
+                for (int u = 0; u < kEntUnroll; ++u) {
+                    const int32_t r = t.find(x[u]);
+                    if (r >= 0) {
+                        ++c;
+                        atomicAdd(tc + r, 1);                                // edge (b, c)
+                        atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);  // edge (a, c)
+                    }
                 }
             }
-        }
-        // the tail (fewer than kEntUnroll * 32 ids): its loads issued together
-        if (j0 < el) {
-            int32_t x[kEntUnroll];
+            // the tail (fewer than kEntUnroll * 32 ids): its loads issued together
+            if (j0 < el) {
+                int32_t x[kEntUnroll];
 #pragma unroll
-            for (int u = 0; u < kEntUnroll; ++u) {
-                const int32_t j = j0 + u * kWarp + lane;
-                x[u] = j < el ? __ldg(fadj + eb + j) : -2;
-            }
+                for (int u = 0; u < kEntUnroll; ++u) {
+                    const int32_t j = j0 + u * kWarp + lane;
+                    x[u] = j < el ? __ldg(xs + eb + j) : -2;
+                }
 #pragma unroll
-            for (int u = 0; u < kEntUnroll; ++u) {
-                if (j0 + u * kWarp >= el) break;  // warp-uniform: no lane has work left
-                const int32_t r = tab_find<LP>(t, x[u]);
-                if (r >= 0) {
-                    ++c;
-                    atomicAdd(t.cnt + r, 1);
-                    atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);
+                for (int u = 0; u < kEntUnroll; ++u) {
+                    if (j0 + u * kWarp >= el) break;  // warp-uniform: no lane has work left
+                    const int32_t r = t.find(x[u]);
+                    if (r >= 0) {
+                        ++c;
+                        atomicAdd(tc + r, 1);
+                        atomicAdd(fcnt + (eb + j0 + u * kWarp + lane), 1);
+                    }
                 }
             }
+            c = __reduce_add_sync(0xffffffffu, c);
+            const uint32_t ef = __shfl_sync(0xffffffffu, def, i);
+            if (lane == 0 && c) atomicAdd(fcnt + ef, c);  // edge (a, b)
         }
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0 && c) atomicAdd(fcnt + e_fin[e], c);  // edge (a, b)
     }
     for (int32_t guard = 0; guard <= nshort; guard += kWarp) {
         int32_t k0 = 0;
@@ -715,13 +800,13 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
             for (int32_t j0 = 0; j0 < el; j0 += 4) {
                 int32_t x[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(fadj + eb + j0 + u) : -2;
+                for (int u = 0; u < 4; ++u) x[u] = j0 + u < el ? __ldg(xs + eb + j0 + u) : -2;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int32_t r = tab_find<LP>(t, x[u]);
+                    const int32_t r = t.find(x[u]);
                     if (r >= 0) {
                         ++c;
-                        atomicAdd(t.cnt + r, 1);
+                        atomicAdd(tc + r, 1);
                         atomicAdd(fcnt + (eb + j0 + u), 1);
                     }
                 }
@@ -732,45 +817,103 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const FTable &t,
 }
 
 // the owner's counts, added to its out-edges (b, c)
-template <bool LP, int BLOCK>
-__device__ __forceinline__ void ent_flush(const FTable &t, const int32_t *__restrict__ fadj, int64_t base,
-                                          int32_t tlen, int32_t *__restrict__ fcnt) {
+template <int BLOCK, class TAB>
+__device__ __forceinline__ void ent_flush(const TAB &t, const int32_t *__restrict__ xs, int64_t base, int32_t tlen,
+                                          int32_t *__restrict__ fcnt) {
+    const int *tc = t.counts();
     for (int k = threadIdx.x; k < tlen; k += BLOCK) {
-        const int32_t r = tab_find<LP>(t, fadj[base + k]);
-        if (r >= 0 && t.cnt[r]) atomicAdd(fcnt + base + k, t.cnt[r]);
+        const int32_t r = t.find(xs[base + k]);
+        if (r >= 0 && tc[r]) atomicAdd(fcnt + base + k, tc[r]);
     }
+}
+
+// Bitmap table of the item's part of out(b) (dense ids xs[base, base+tlen)):
+// clear, set the bits, then each word's prefix count, by warps walking
+// consecutive words (lane l on word w0 + 32j + l: no bank conflicts).
+template <int BLOCK>
+__device__ __forceinline__ void bit_build(const BitTab &t, const int32_t *__restrict__ xs, int64_t base,
+                                          int32_t tlen, int32_t *wtot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kW = BLOCK / 32;
+    const int32_t nw = (int32_t)((t.span + 15u) >> 4);
+    for (int k = threadIdx.x; k < nw; k += BLOCK) t.w[k] = 0u;
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) t.cnt[k] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+        const uint32_t r = (uint32_t)(xs[base + k] - t.lo);
+        atomicOr(t.w + (r >> 4), 1u << (r & 15u));
+    }
+    __syncthreads();
+    const int32_t per = ((nw + kW - 1) / kW + 31) & ~31;
+    const int32_t w0 = min(nw, wid * per), w1 = min(nw, w0 + per);
+    int tot = 0;
+    for (int32_t k = w0 + lane; k < w1; k += kWarp) tot += __popc(t.w[k]);
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    if (lane == 0) wtot[wid] = tot;
+    __syncthreads();
+    int acc = 0;
+    for (int j = 0; j < wid; ++j) acc += wtot[j];
+    for (int32_t k0 = w0; k0 < w1; k0 += kWarp) {
+        const int32_t k = k0 + lane;
+        const uint32_t y = k < w1 ? t.w[k] : 0u;
+        const int c = __popc(y);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += z;
+        }
+        if (k < w1) t.w[k] = y | ((uint32_t)(acc + inc - c) << 16);
+        acc += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncthreads();
 }
 
 // One CTA per item, streaming its precomputed entries. A hit c adds one to
 // (b, c) in the table, to (a, c) at the streamed slot in global memory, and
 // -- summed over the entry -- to (a, b). Dynamic shared memory: the table
-// (2^cap_logs keys, then 2^cap_logs counts).
+// (2^cap_logs keys, then 2^cap_logs counts; or, for a bitmap item, the
+// bitmap words, then one count per element).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ items, const int64_t *__restrict__ foff,
                                                    const int32_t *__restrict__ fadj,
+                                                   const int32_t *__restrict__ fhid,
                                                    const int32_t *__restrict__ e_base,
                                                    const int32_t *__restrict__ e_len,
                                                    const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
                                                    int cap_logs, int load_shift) {
     extern __shared__ int tsm[];
     __shared__ int32_t next_long, next_short, failed;
+    __shared__ int32_t wtot[BLOCK / 32];
     const FItem it = items[blockIdx.x];
     const int32_t b = it.v;
     const int64_t fb = foff[b];
     const int32_t ob = (int32_t)(foff[b + 1] - fb);
     const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
-    FTable t;
-    t.logs = min(cap_logs, max(5, fceil_log2(tlen << load_shift)));
-    t.keys = tsm;
-    t.cnt = tsm + (1 << cap_logs);
-    for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) {
-        t.keys[k] = -1;
-        t.cnt[k] = 0;
-    }
     if (threadIdx.x == 0) {
         next_long = 0;
         next_short = 0;
         failed = 0;
+    }
+    if (it.hspan > 0) {
+        BitTab t;
+        t.w = (uint32_t *)tsm;
+        t.lo = it.hlo;
+        t.span = (uint32_t)it.hspan;
+        t.cnt = tsm + ((t.span + 15u) >> 4);
+        bit_build<BLOCK>(t, fhid, fb + tb, tlen, wtot);
+        ent_stream(it, t, fhid, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+        __syncthreads();
+        ent_flush<BLOCK>(t, fhid, fb + tb, tlen, fcnt);
+        return;
+    }
+    FTable t;
+    t.logs = min(cap_logs, max(5, fceil_log2(tlen << load_shift)));
+    t.keys = tsm;
+    t.cnt = tsm + (1 << t.logs);
+    for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) {
+        t.keys[k] = -1;
+        t.cnt[k] = 0;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < tlen; k += BLOCK)
@@ -781,13 +924,15 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
         __syncthreads();
         for (int k = threadIdx.x; k < tlen; k += BLOCK) lp_insert(t, fadj[fb + tb + k]);
         __syncthreads();
-        ent_stream<true>(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+        const HashTab<true> h{t};
+        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
         __syncthreads();
-        ent_flush<true, BLOCK>(t, fadj, fb + tb, tlen, fcnt);
+        ent_flush<BLOCK>(h, fadj, fb + tb, tlen, fcnt);
     } else {
-        ent_stream<false>(it, t, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
+        const HashTab<false> h{t};
+        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
         __syncthreads();
-        ent_flush<false, BLOCK>(t, fadj, fb + tb, tlen, fcnt);
+        ent_flush<BLOCK>(h, fadj, fb + tb, tlen, fcnt);
     }
 }
 
@@ -932,10 +1077,70 @@ __global__ void k_fwd_src(const uint32_t *__restrict__ oe, int64_t m, const int3
         fsrc[i] = src[oe[i]];
 }
 
+// Dense ids of the bitmap tables: vertices ordered by degree level
+// (floor(log2 deg)), highest level first, then by id (isolated vertices get
+// none). A stable partition by level over tiles of kHidTile ids: per-tile
+// level counts, one exclusive scan over them laid out level-major (highest
+// level first), then each vertex's place among its tile's vertices of the
+// same level.
+constexpr int kHidTile = 256;
+
+__device__ __forceinline__ int deg_level(int32_t d) { return 31 - __clz(d); }  // d >= 1
+
+__global__ void __launch_bounds__(kHidTile) k_hid_count(const int32_t *__restrict__ deg, int32_t n, int64_t ntiles,
+                                                         int32_t *__restrict__ tcnt) {
+    __shared__ int32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * kHidTile + threadIdx.x;
+    const int32_t d = v < n ? deg[v] : 0;
+    if (d > 0) atomicAdd(&h[deg_level(d)], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) tcnt[(int64_t)(31 - threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kHidTile) k_hid_assign(const int32_t *__restrict__ deg, int32_t n, int64_t ntiles,
+                                                          const int64_t *__restrict__ toff,
+                                                          int32_t *__restrict__ vhid) {
+    __shared__ int32_t wc[kHidTile / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kHidTile; k += kHidTile) (&wc[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * kHidTile + threadIdx.x;
+    const int32_t d = v < n ? deg[v] : 0;
+    const int L = d > 0 ? deg_level(d) : 32;  // 32: no dense id
+    const unsigned same = __match_any_sync(0xffffffffu, L);
+    const int below = __popc(same & ((1u << lane) - 1u));
+    if (L < 32 && below == 0) wc[wid][L] = __popc(same);
+    __syncthreads();
+    if (v >= n) return;
+    if (L == 32) {
+        vhid[v] = -1;
+        return;
+    }
+    int32_t before = 0;
+    for (int j = 0; j < wid; ++j) before += wc[j][L];
+    vhid[v] = (int32_t)(toff[(int64_t)(31 - L) * ntiles + blockIdx.x] + before + below);
+}
+
+__global__ void k_fwd_hid(const int32_t *__restrict__ fadj, int64_t m, const int32_t *__restrict__ vhid,
+                          int32_t *__restrict__ fhid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        fhid[i] = vhid[fadj[i]];
+}
+
 // CTA item classes by the owner's out-degree: 0 up to 256 (128-thread CTAs,
 // 8 KB tables), 1 up to 1024 (512 threads, 32 KB), 2 above (512 threads,
 // tables of 4096-key chunks, 128 KB)
 __host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
+
+// log2 of the hash slots of a class's tables (8 bytes per slot: 8, 32 and
+// 128 KB); a bitmap table must fit the same shared memory
+__host__ __device__ __forceinline__ int fwd_cap_logs(int cls) { return cls == 0 ? 10 : (cls == 1 ? 12 : 14); }
+
+// hash slots per key, as a shift: 2^3 in class 1 (load <= 1/8 up to 512
+// keys), 2^2 in classes 0 and 2
+__host__ __device__ __forceinline__ int fwd_load_shift(int cls) { return cls == 1 ? 3 : 2; }
 
 // warp per vertex: work as a middle vertex and the number of items
 __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restrict__ off,
@@ -991,7 +1196,7 @@ __global__ void k_fwd_sched_write(const int32_t *__restrict__ deg, const int64_t
     FItem *dst = cls == 0 ? i0 : (cls == 1 ? i1 : i2);
     unsigned long long p = atomicAdd(cursor + 1 + cls, (unsigned long long)(nchunks * nr));
     for (int32_t c = 0; c < nchunks; ++c)
-        for (int32_t r = 0; r < nr; ++r) dst[p++] = FItem{(int32_t)b, c, r * len, min(db, (r + 1) * len), 0, 0, 0};
+        for (int32_t r = 0; r < nr; ++r) dst[p++] = FItem{(int32_t)b, c, r * len, min(db, (r + 1) * len), 0, 0, 0, 0, 0};
 }
 
 }  // namespace
@@ -1076,7 +1281,7 @@ static scan_status fwd_build_entries(Graph *g) {
         dev_free(c, nent);
         for (auto &b : eoff) dev_free(c, b);
     };
-    SCAN_TRY(dev_alloc(c, nent, 4 * (size_t)nmax));
+    SCAN_TRY(dev_alloc(c, nent, 4 * (size_t)std::max<int64_t>(nmax, 3)));
     for (int cls = 0; cls < 3; ++cls) {
         const int64_t ni = g->fwd_items_n[cls];
         if (ni == 0) continue;
@@ -1111,6 +1316,10 @@ static scan_status fwd_build_entries(Graph *g) {
         set_error("");
         return SCAN_OK;  // no room: per-round entries
     }
+    // the largest table of each class, so each launch takes only the shared
+    // memory it needs (the rest stays L1 cache for the streamed lists)
+    int32_t *need = (int32_t *)nent.ptr;  // the entry counts are no longer needed
+    SCAN_CUDA(cudaMemsetAsync(need, 0, 3 * sizeof(int32_t), c->stream));
     for (int cls = 0; cls < 3; ++cls) {
         const int64_t ni = g->fwd_items_n[cls];
         const int64_t first = cls == 0 ? 0 : (cls == 1 ? total[0] : total[0] + total[1]);
@@ -1118,15 +1327,59 @@ static scan_status fwd_build_entries(Graph *g) {
         k_fwd_ent_write<<<(unsigned)ni, 256, 0, c->stream>>>(
             (FItem *)g->fwd_items[cls].ptr, ni, (const int64_t *)eoff[cls].ptr, first, off, adj,
             deg, foff, fadj, fin, rs, (int32_t *)g->fwd_ebase.ptr, (int32_t *)g->fwd_elen.ptr,
-            (uint32_t *)g->fwd_efin.ptr);
+            (uint32_t *)g->fwd_efin.ptr, (const int32_t *)g->fhid.ptr, 2 << fwd_cap_logs(cls), fwd_cap_logs(cls),
+            fwd_load_shift(cls), need + cls);
         c->launches++;
     }
+    int32_t hneed[3] = {0, 0, 0};
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hneed, need, sizeof(hneed), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    for (int cls = 0; cls < 3; ++cls) g->fwd_smem_words[cls] = hneed[cls];
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "forward entries");
     g->fwd_entries = true;
     return SCAN_OK;
+}
+
+// Dense ids of the out-list elements (Graph::fhid) for the bitmap tables.
+// Without room for them under the budget every owner keeps a hash table.
+static scan_status fwd_build_hid(Graph *g) {
+    Ctx *c = g->ctx;
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    if (dev_alloc(c, g->fhid, 4 * (size_t)m) != SCAN_OK) {
+        set_error("");
+        return SCAN_OK;
+    }
+    const int64_t ntiles = ((int64_t)n + kHidTile - 1) / kHidTile;
+    DevBuf tcnt, toff;
+    if (dev_alloc(c, tcnt, 4 * (size_t)(32 * ntiles)) != SCAN_OK ||
+        dev_alloc(c, toff, 8 * (size_t)(32 * ntiles + 1)) != SCAN_OK) {
+        dev_free(c, tcnt);
+        dev_free(c, toff);
+        dev_free(c, g->fhid);
+        set_error("");
+        return SCAN_OK;
+    }
+    auto *deg = (const int32_t *)g->deg.ptr;
+    int32_t *vhid = (int32_t *)g->parent.ptr;  // scratch int32[n+1] (free until the query's later stages)
+    k_hid_count<<<(unsigned)ntiles, kHidTile, 0, c->stream>>>(deg, n, ntiles, (int32_t *)tcnt.ptr);
+    c->launches++;
+    scan_status s = launch_exclusive_scan_i32_to_i64(c, (const int32_t *)tcnt.ptr, (int64_t *)toff.ptr, 32 * ntiles,
+                                                     g->scan_tmp);
+    if (s == SCAN_OK) {
+        k_hid_assign<<<(unsigned)ntiles, kHidTile, 0, c->stream>>>(deg, n, ntiles, (const int64_t *)toff.ptr, vhid);
+        k_fwd_hid<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>((const int32_t *)g->fadj.ptr, m, vhid,
+                                                                             (int32_t *)g->fhid.ptr);
+        c->launches += 2;
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = cuda_fail(e, "dense ids");
+    }
+    dev_free(c, tcnt);
+    dev_free(c, toff);
+    if (s != SCAN_OK) dev_free(c, g->fhid);
+    return s;
 }
 
 scan_status fwd_prepare(Graph *g) {
@@ -1196,6 +1449,11 @@ scan_status fwd_prepare(Graph *g) {
         k_fwd_src<<<grid_for(m, 256, c->num_sms * 32), 256, 0, c->stream>>>(
             (const uint32_t *)g->oe.ptr, m, (const int32_t *)g->src.ptr, (int32_t *)g->fsrc.ptr);
         c->launches++;
+        const scan_status hs = fwd_build_hid(g);
+        if (hs != SCAN_OK) {
+            dev_free(c, cnts);
+            return hs;
+        }
     }
     // schedule (rebuilt alone when the autotuner changes its parameters)
     SCAN_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), c->stream));
@@ -1244,6 +1502,7 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     auto *fadj = (const int32_t *)g->fadj.ptr;
     auto *fin = (const uint32_t *)g->fin.ptr;
     auto *fcnt = (int32_t *)g->fcnt.ptr;
+    auto *fhid = (const int32_t *)g->fhid.ptr;
     // entry lists: built on the first count of the default family (not for
     // the lean one, and not again after they did not fit the budget)
     const bool lean = g->strategy == SCAN_STRATEGY_FORWARD_LEAN;
@@ -1263,20 +1522,21 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
             // and small CTAs wait less at their barriers). Class 1: eight slots
             // per key up to 512 keys, four above, 32 KB (four 512-thread CTAs
             // per SM). Class 2: four per key, 128 KB.
-            const int cap_logs = cls == 0 ? 10 : (cls == 1 ? 12 : 14), load_shift = cls == 1 ? 3 : 2;
-            const size_t smem = (size_t)(2 * sizeof(int)) << cap_logs;
+            const int cap_logs = fwd_cap_logs(cls), load_shift = fwd_load_shift(cls);
+            const size_t full = (size_t)(2 * sizeof(int)) << cap_logs;
+            const size_t smem = g->fwd_smem_words[cls] > 0 ? std::min(full, 4 * (size_t)g->fwd_smem_words[cls]) : full;
             auto *items = (const FItem *)g->fwd_items[cls].ptr;
             auto *eb = (const int32_t *)g->fwd_ebase.ptr;
             auto *el = (const int32_t *)g->fwd_elen.ptr;
             auto *ef = (const uint32_t *)g->fwd_efin.ptr;
             if (cls == 0) {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<128><<<(unsigned)ni, 128, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
-                                                                load_shift);
+                k_fwd_ent<128><<<(unsigned)ni, 128, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                                                                cap_logs, load_shift);
             } else {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, eb, el, ef, fcnt, cap_logs,
-                                                                load_shift);
+                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                                                                cap_logs, load_shift);
             }
             c->launches++;
         }

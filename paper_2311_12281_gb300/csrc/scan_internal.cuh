@@ -66,6 +66,7 @@ struct Graph {
     DevBuf fin;             // uint32[nnz] for a slot (b, a) with a below b: index of a->b in fadj
     DevBuf fcnt;            // int32[m] triangle counts per oriented edge
     DevBuf fsrc;            // int32[m] lower endpoint of each oriented edge, in fadj order
+    DevBuf fhid;            // int32[m] dense id of each out-list element (degree level first): bitmap tables
     DevBuf fwd_owners;      // warp-level owners
     DevBuf fwd_items[3];    // CTA items, by table class 1..2
     int64_t fwd_items_n[3] = {0, 0, 0};
@@ -75,6 +76,7 @@ struct Graph {
     bool fwd_entries = false;              // entries built (else the kernel derives them per round)
     bool fwd_entries_tried = false;        // a build was attempted (it is skipped when it does not fit)
     bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
+    int32_t fwd_smem_words[3] = {0, 0, 0};  // shared memory the largest table of each item class needs
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
@@ -110,7 +112,7 @@ struct Graph {
     template <class F>
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &cdd, &owners_small, &items[0], &items[1],
-                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fwd_owners,
+                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fhid, &fwd_owners,
                           &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
                           &qparams, &sim, &simo, &nsim, &hst, &mslots, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
@@ -161,6 +163,7 @@ struct Ctx {
     uint64_t launches = 0;
     int num_sms = 0;
     int smem_optin = 0;
+    uint32_t loop_limit = 0;  // union-find iteration cap of later queries; 0 = the compiled bound
     // per-stage timing
     bool profiling = false;
     std::vector<StageMark> marks;
@@ -231,6 +234,7 @@ scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32
 scan_status part_query(Graph *g, const scan_params &p, scan_result **out);
 void part_release(Graph *g);
 int32_t part_block_count(const Graph *g);
+uint64_t part_transfer_bytes(const Graph *g);
 
 #define SCAN_CUDA(call)                                              \
     do {                                                             \
