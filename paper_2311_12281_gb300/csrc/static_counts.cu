@@ -12,19 +12,13 @@
 //
 // The kernel is the per-edge binary-search count (the library's plain
 // comparator kernel) with its scratch moved into that array.
-#include <mutex>
-
 #include "scan_internal.cuh"
 
 namespace {
 
 constexpr size_t kStaticBytes = 64ull << 20;  // 64 MiB of device scratch
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
-
-std::mutex g_setup_mu;
-unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -123,25 +117,17 @@ extern "C" scan_status scan_common_counts_static(const int64_t *offsets, const i
                   std::to_string(kStaticBytes) + " available (about n + 2*nnz <= 16.7M entries)");
         return SCAN_EINVAL;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return scan::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device ordinal out of range");
-        return SCAN_EINVAL;
-    }
+    // The host-side symbol is only a stand-in; the array's device address on
+    // the current device comes from the runtime. It is looked up on every
+    // call (a host-side table lookup once the module is loaded), so a device
+    // or context reset, which reloads the module at a new address, can never
+    // leave a stale address behind.
     unsigned char *base = nullptr;
     {
-        // Once per device, with that device current: the host-side symbol is
-        // only a stand-in; the device address comes from the runtime.
-        std::lock_guard<std::mutex> lock(g_setup_mu);
-        if (!g_scratch_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_static_scratch);
-            if (e != cudaSuccess) return scan::cuda_fail(e, "cudaGetSymbolAddress");
-            g_scratch_ptr[dev] = (unsigned char *)p;
-        }
-        base = g_scratch_ptr[dev];
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return scan::cuda_fail(e, "cudaGetSymbolAddress");
+        base = (unsigned char *)p;
     }
     cudaStream_t st = (cudaStream_t)stream;
     auto *bad = (unsigned long long *)base;
