@@ -1,7 +1,9 @@
-// autotune.cu -- choose the similarity kernel family and the forward
-// schedule's work sizes by timing them on the graph, and remember the choice
-// per graph shape in a plain text file (one line per choice: key, strategy,
-// warp-owner work bound, CTA item work, milliseconds).
+// autotune.cu -- choose the similarity kernel family, the forward
+// schedule's work sizes and its launch form (one launch per item class, or
+// one persistent launch over a work queue) by timing them on the graph, and
+// remember the choice per graph shape in a plain text file (one line per
+// choice: "fwd2", key, strategy, warp-owner work bound, CTA item work, queue,
+// milliseconds).
 //
 // A graph's shape key is (floor log2 n, floor log2 nnz, floor log2 max
 // degree): graphs with the same key reuse a stored choice without timing.
@@ -26,6 +28,7 @@ struct Choice {
     int strategy = SCAN_STRATEGY_FORWARD;
     int64_t small_work = 1 << 15;
     int64_t item_work = 1 << 20;
+    int queue = 0;
     double ms = 0;
 };
 
@@ -50,6 +53,7 @@ void reset_forward_schedule(Graph *g) {
 scan_status apply(Graph *g, const Choice &ch) {
     query_graph_drop(g);
     g->strategy = ch.strategy;
+    g->fwd_queue = ch.queue != 0;
     if (ch.strategy == SCAN_STRATEGY_FORWARD &&
         (g->fwd_small_work != ch.small_work || g->fwd_item_work != ch.item_work)) {
         g->fwd_small_work = ch.small_work;
@@ -82,16 +86,19 @@ bool load_choice(const char *path, const std::string &key, Choice *out) {
     if (!path || !*path) return false;
     FILE *f = fopen(path, "r");
     if (!f) return false;
-    char k[128];
-    int strat;
+    char line[512], tag[16], k[128];
+    int strat, queue;
     long long sw, iw;
     double ms;
     bool found = false;
-    while (fscanf(f, "%127s %d %lld %lld %lf", k, &strat, &sw, &iw, &ms) == 5) {
-        if (key == k) {
+    while (fgets(line, sizeof(line), f)) {
+        // lines of another format are skipped
+        if (sscanf(line, "%15s %127s %d %lld %lld %d %lf", tag, k, &strat, &sw, &iw, &queue, &ms) != 7) continue;
+        if (std::string(tag) == "fwd2" && key == k) {
             out->strategy = strat;
             out->small_work = sw;
             out->item_work = iw;
+            out->queue = queue;
             out->ms = ms;
             found = true;  // the last matching line wins
         }
@@ -104,8 +111,8 @@ void store_choice(const char *path, const std::string &key, const Choice &ch) {
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %lld %lld %.9g\n", key.c_str(), ch.strategy, (long long)ch.small_work,
-            (long long)ch.item_work, ch.ms);
+    fprintf(f, "fwd2 %s %d %lld %lld %d %.9g\n", key.c_str(), ch.strategy, (long long)ch.small_work,
+            (long long)ch.item_work, ch.queue, ch.ms);
     fclose(f);
 }
 
@@ -148,13 +155,15 @@ extern "C" scan_status scan_graph_autotune(scan_graph *g, const char *cache_path
             const bool had_cache = g->cache_valid;
             std::vector<Choice> cands;
             for (int64_t iw : {int64_t(1) << 18, int64_t(1) << 20, int64_t(1) << 22})
-                for (int64_t sw : {int64_t(1) << 12, int64_t(1) << 15}) {
-                    Choice ch;
-                    ch.strategy = SCAN_STRATEGY_FORWARD;
-                    ch.item_work = iw;
-                    ch.small_work = sw;
-                    cands.push_back(ch);
-                }
+                for (int64_t sw : {int64_t(1) << 12, int64_t(1) << 15})
+                    for (int queue : {0, 1}) {
+                        Choice ch;
+                        ch.strategy = SCAN_STRATEGY_FORWARD;
+                        ch.item_work = iw;
+                        ch.small_work = sw;
+                        ch.queue = queue;
+                        cands.push_back(ch);
+                    }
             Choice own;
             own.strategy = SCAN_STRATEGY_OWNER;
             cands.push_back(own);

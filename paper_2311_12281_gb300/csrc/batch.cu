@@ -170,7 +170,7 @@ scan_status batch_query_to_device(scan_batch *b, const scan_params *params, uint
         SCAN_CUDA(cudaMemcpyAsync(b->gmu.ptr, b->h_mu, 4 * (size_t)b->k, cudaMemcpyHostToDevice, c->stream));
         return query_pipeline(b->g, qp, mode, core, cid, label, pairs, pairs_cap, npairs);
     };
-    const bool replayable = !(mode & SCAN_Q_BUILD_CACHE) && !c->profiling && !b->graph_off;
+    const bool replayable = !(mode & SCAN_Q_BUILD_CACHE) && !c->profiling && !b->graph_off && !c->loop_limit;
     const uint64_t key = replay_key(mode | (b->g->cache_valid ? 0x100u : 0u), core, cid, label, pairs, pairs_cap,
                                     npairs);
     if (replayable && b->exec && b->key == key) {
@@ -318,6 +318,10 @@ scan_status batch_create(Ctx *ctx, int32_t k, const int32_t *ns, const int64_t *
         const scan_status gs = graph_create(ctx, (int32_t)n, nullptr, nullptr, nnz, false, &b->g, fill);
         free_tmp();
         if (gs != SCAN_OK) return fail(gs);
+        // a union of many small graphs holds mostly small owners: one
+        // persistent launch over the work queue counts it (the autotuner may
+        // still choose otherwise)
+        b->g->fwd_queue = true;
     }
     // parameter and result staging from the pinned pool (reused by the next batch)
     b->h_pp = (uint64_t *)pinned_get(8 * (size_t)k, &b->cap[0]);

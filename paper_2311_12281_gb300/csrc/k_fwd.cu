@@ -35,6 +35,19 @@ constexpr int kFwdChunk = 4096;          // max out(b) elements per CTA table
 constexpr int kFwdUnroll = 8;
 constexpr unsigned long long kSlotEmpty = ~0ull;
 
+// CTA item classes by the owner's out-degree: 0 up to 256 (128-thread CTAs,
+// 8 KB tables), 1 up to 1024 (512 threads, 32 KB), 2 above (512 threads,
+// tables of 4096-key chunks, 128 KB)
+__host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
+
+// log2 of the hash slots of a class's tables (8 bytes per slot: 8, 32 and
+// 128 KB); a bitmap table must fit the same shared memory
+__host__ __device__ __forceinline__ int fwd_cap_logs(int cls) { return cls == 0 ? 10 : (cls == 1 ? 12 : 14); }
+
+// hash slots per key, as a shift: 2^3 in class 1 (load <= 1/8 up to 512
+// keys), 2^2 in classes 0 and 2
+__host__ __device__ __forceinline__ int fwd_load_shift(int cls) { return cls == 1 ? 3 : 2; }
+
 // A CTA work item: owner v, value chunk of out(v), slot range [sb, se) of
 // v's row; with precomputed entry lists, the item's entries start at e0 (the
 // nlong long ones first, then the short ones). hspan > 0: the owner's table
@@ -147,6 +160,70 @@ __device__ __forceinline__ int probe_run(const int32_t *__restrict__ row, int32_
 }
 
 // ------------------------------------------------------------ warp owners
+// One warp-level owner b (out-degree <= 64): a linear-probing hash table of
+// out(b) with a membership filter in front, in the warp's own shared memory
+// (t: kFwdSmallTable slots, bm: 64 words, ocnt: kFwdSmallOut counts); every
+// in-neighbour a below b streams its part of out(a) through it.
+__device__ __forceinline__ void fwd_small_owner(int32_t b, unsigned long long *t, uint32_t *bm, int32_t *ocnt,
+                                                const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                const int32_t *__restrict__ deg, const int64_t *__restrict__ foff,
+                                                const int32_t *__restrict__ fadj, const uint32_t *__restrict__ fin,
+                                                int32_t *__restrict__ fcnt, int rank_sorted) {
+    const int lane = threadIdx.x & 31;
+    const int64_t fb = foff[b];
+    const int32_t db = deg[b], ob = (int32_t)(foff[b + 1] - fb);
+    const int logc = max(5, fceil_log2(4 * ob));
+    const int logb = max(5, fceil_log2(32 * ob));  // <= 2048 bits
+    for (int k = lane; k < (1 << logc); k += kWarp) t[k] = kSlotEmpty;
+    for (int k = lane; k < (1 << (logb - 5)); k += kWarp) bm[k] = 0u;
+    for (int k = lane; k < kFwdSmallOut; k += kWarp) ocnt[k] = 0;
+    __syncwarp();
+    for (int k = lane; k < ob; k += kWarp) {
+        const int32_t x = fadj[fb + k];
+        ftab_insert(t, logc, x, k);
+        fbits_set(bm, logb, x);
+    }
+    __syncwarp();
+    const int64_t rb = off[b];
+    for (int32_t g0 = 0; g0 < db; g0 += kWarp) {
+        const int64_t s = rb + g0 + lane;
+        int32_t oa = 0, st = 0;
+        int64_t fa = 0;
+        if (g0 + lane < db) {
+            const int32_t a = adj[s];
+            const int32_t da = deg[a];
+            if (dev::rank_less(da, a, db, b)) {
+                fa = foff[a];
+                oa = (int32_t)(foff[a + 1] - fa);
+                // a rank-sorted out(a) holds b's common neighbours above b only
+                if (rank_sorted) st = (int32_t)((int64_t)fin[s] - fa) + 1;
+            }
+        }
+        const int32_t len = oa - st;
+        int mine = 0;
+        if (len > 0 && len < 16) mine = probe_run<4>(fadj + fa, fcnt + fa, st, oa, 1, t, logc, bm, logb, ocnt);
+        unsigned longs = __ballot_sync(0xffffffffu, len >= 16);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t fas = __shfl_sync(0xffffffffu, fa, src);
+            const int32_t oas = __shfl_sync(0xffffffffu, oa, src);
+            const int32_t sts = __shfl_sync(0xffffffffu, st, src);
+            int c = probe_run<kFwdUnroll>(fadj + fas, fcnt + fas, sts + lane, oas, kWarp, t, logc, bm, logb, ocnt);
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (lane == src) mine = c;
+        }
+        if (oa > 0 && mine) atomicAdd(fcnt + fin[s], mine);
+    }
+    __syncwarp();
+    for (int k = lane; k < ob; k += kWarp)
+        if (ocnt[k]) atomicAdd(fcnt + fb + k, ocnt[k]);
+    __syncwarp();
+}
+
+// shared memory of one warp-level owner: table, filter, counts (in 32-bit words)
+constexpr int kSmallWarpWords = 2 * kFwdSmallTable + 64 + kFwdSmallOut;
+
 __global__ void __launch_bounds__(256) k_fwd_small(const int32_t *__restrict__ owners, int32_t nown,
                                                    const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                                    const int32_t *__restrict__ deg, const int64_t *__restrict__ foff,
@@ -155,65 +232,11 @@ __global__ void __launch_bounds__(256) k_fwd_small(const int32_t *__restrict__ o
     __shared__ unsigned long long tables[8][kFwdSmallTable];
     __shared__ uint32_t bitmaps[8][64];
     __shared__ int32_t ocnts[8][kFwdSmallOut];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long *t = tables[wid];
-    uint32_t *bm = bitmaps[wid];
-    int32_t *ocnt = ocnts[wid];
+    const int wid = threadIdx.x >> 5;
     const int warps_total = gridDim.x * 8;
-    for (int32_t i = blockIdx.x * 8 + wid; i < nown; i += warps_total) {
-        const int32_t b = owners[i];
-        const int64_t fb = foff[b];
-        const int32_t db = deg[b], ob = (int32_t)(foff[b + 1] - fb);
-        const int logc = max(5, fceil_log2(4 * ob));
-        const int logb = max(5, fceil_log2(32 * ob));  // <= 2048 bits
-        for (int k = lane; k < (1 << logc); k += kWarp) t[k] = kSlotEmpty;
-        for (int k = lane; k < (1 << (logb - 5)); k += kWarp) bm[k] = 0u;
-        for (int k = lane; k < kFwdSmallOut; k += kWarp) ocnt[k] = 0;
-        __syncwarp();
-        for (int k = lane; k < ob; k += kWarp) {
-            const int32_t x = fadj[fb + k];
-            ftab_insert(t, logc, x, k);
-            fbits_set(bm, logb, x);
-        }
-        __syncwarp();
-        const int64_t rb = off[b];
-        for (int32_t g0 = 0; g0 < db; g0 += kWarp) {
-            const int64_t s = rb + g0 + lane;
-            int32_t oa = 0, st = 0;
-            int64_t fa = 0;
-            if (g0 + lane < db) {
-                const int32_t a = adj[s];
-                const int32_t da = deg[a];
-                if (dev::rank_less(da, a, db, b)) {
-                    fa = foff[a];
-                    oa = (int32_t)(foff[a + 1] - fa);
-                    // a rank-sorted out(a) holds b's common neighbours above b only
-                    if (rank_sorted) st = (int32_t)((int64_t)fin[s] - fa) + 1;
-                }
-            }
-            const int32_t len = oa - st;
-            int mine = 0;
-            if (len > 0 && len < 16)
-                mine = probe_run<4>(fadj + fa, fcnt + fa, st, oa, 1, t, logc, bm, logb, ocnt);
-            unsigned longs = __ballot_sync(0xffffffffu, len >= 16);
-            while (longs) {
-                const int src = __ffs(longs) - 1;
-                longs &= longs - 1;
-                const int64_t fas = __shfl_sync(0xffffffffu, fa, src);
-                const int32_t oas = __shfl_sync(0xffffffffu, oa, src);
-                const int32_t sts = __shfl_sync(0xffffffffu, st, src);
-                int c = probe_run<kFwdUnroll>(fadj + fas, fcnt + fas, sts + lane, oas, kWarp, t, logc, bm, logb,
-                                              ocnt);
-                c = __reduce_add_sync(0xffffffffu, c);
-                if (lane == src) mine = c;
-            }
-            if (oa > 0 && mine) atomicAdd(fcnt + fin[s], mine);
-        }
-        __syncwarp();
-        for (int k = lane; k < ob; k += kWarp)
-            if (ocnt[k]) atomicAdd(fcnt + fb + k, ocnt[k]);
-        __syncwarp();
-    }
+    for (int32_t i = blockIdx.x * 8 + wid; i < nown; i += warps_total)
+        fwd_small_owner(owners[i], tables[wid], bitmaps[wid], ocnts[wid], off, adj, deg, foff, fadj, fin, fcnt,
+                        rank_sorted);
 }
 
 // ------------------------------------------------------------ CTA owners
@@ -580,16 +603,17 @@ __global__ void __launch_bounds__(256) k_fwd_ent_write(FItem *__restrict__ items
         it.nlong = nlong;
         it.nent = acc;
         // 16 ids per 32-bit word (the high half holds the word's prefix
-        // count), then one count per element of the part of out(b)
+        // count) through the word of id span, then one count per element of
+        // the part of out(b)
         it.hlo = 0;
         it.hspan = 0;
         int32_t words = 2 << min(cap_logs, max(5, fceil_log2(tlen << load_shift)));  // hash: keys and counts
         if (fhid != nullptr && hmax >= hmin && hmax != INT32_MAX) {
             const int64_t span = (int64_t)hmax - hmin + 1;
-            if ((span + 15) / 16 + tlen <= (int64_t)cap_words) {
+            if (span / 16 + 1 + tlen <= (int64_t)cap_words) {
                 it.hlo = hmin;
                 it.hspan = (int32_t)span;
-                words = (int32_t)((span + 15) / 16 + tlen);
+                words = (int32_t)(span / 16 + 1 + tlen);
             }
         }
         atomicMax(need_words, words);
@@ -702,10 +726,11 @@ struct BitTab {
     int32_t lo;
     uint32_t span;
     __device__ __forceinline__ int32_t find(int32_t x) const {
-        const uint32_t r = (uint32_t)(x - lo);  // -2 padding and ids below lo wrap above span
-        if (r >= span) return -1;
-        const uint32_t y = w[r >> 4], s = r & 15u;
-        return ((y >> s) & 1u) ? (int32_t)((y >> 16) + __popc(y & ((1u << s) - 1u))) : -1;
+        // -2 padding and ids below lo wrap above span; every id at or past the
+        // span reads the zero word after the bitmap, so no branch is needed
+        const uint32_t r = min((uint32_t)(x - lo), span);
+        const uint32_t y = w[r >> 4], bit = 1u << (r & 15u);
+        return (y & bit) ? (int32_t)((y >> 16) + __popc(y & (bit - 1u))) : -1;
     }
     __device__ __forceinline__ int *counts() const { return cnt; }
 };
@@ -816,12 +841,32 @@ __device__ __forceinline__ void ent_stream(const FItem &it, const TAB &t, const 
     }
 }
 
+// A team of threads that builds and streams one owner table: the whole CTA,
+// or a quarter of it in the persistent kernel, synchronised by its own
+// named barrier (1 + id; barrier 0 is __syncthreads).
+template <int SIZE, bool WHOLE>
+struct Team {
+    static constexpr int size = SIZE;
+    int tid, id;
+    __device__ __forceinline__ void sync() const {
+        if (WHOLE) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(1 + id), "r"(SIZE) : "memory");
+    }
+};
+
+// Shared counters of a team: long and short entries taken, a failed cuckoo
+// chain, and the per-warp totals of the bitmap prefix counts.
+struct TeamVars {
+    int32_t next_long, next_short, failed;
+    int32_t wtot[16];
+};
+
 // the owner's counts, added to its out-edges (b, c)
-template <int BLOCK, class TAB>
-__device__ __forceinline__ void ent_flush(const TAB &t, const int32_t *__restrict__ xs, int64_t base, int32_t tlen,
-                                          int32_t *__restrict__ fcnt) {
+template <class TEAM, class TAB>
+__device__ __forceinline__ void ent_flush(const TEAM &tm, const TAB &t, const int32_t *__restrict__ xs, int64_t base,
+                                          int32_t tlen, int32_t *__restrict__ fcnt) {
     const int *tc = t.counts();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+    for (int k = tm.tid; k < tlen; k += tm.size) {
         const int32_t r = t.find(xs[base + k]);
         if (r >= 0 && tc[r]) atomicAdd(fcnt + base + k, tc[r]);
     }
@@ -830,27 +875,27 @@ __device__ __forceinline__ void ent_flush(const TAB &t, const int32_t *__restric
 // Bitmap table of the item's part of out(b) (dense ids xs[base, base+tlen)):
 // clear, set the bits, then each word's prefix count, by warps walking
 // consecutive words (lane l on word w0 + 32j + l: no bank conflicts).
-template <int BLOCK>
-__device__ __forceinline__ void bit_build(const BitTab &t, const int32_t *__restrict__ xs, int64_t base,
-                                          int32_t tlen, int32_t *wtot) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kW = BLOCK / 32;
-    const int32_t nw = (int32_t)((t.span + 15u) >> 4);
-    for (int k = threadIdx.x; k < nw; k += BLOCK) t.w[k] = 0u;
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) t.cnt[k] = 0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK) {
+template <class TEAM>
+__device__ __forceinline__ void bit_build(const TEAM &tm, const BitTab &t, const int32_t *__restrict__ xs,
+                                          int64_t base, int32_t tlen, int32_t *wtot) {
+    const int lane = tm.tid & 31, wid = tm.tid >> 5;
+    constexpr int nwarps = TEAM::size >> 5;
+    const int32_t nw = (int32_t)(t.span >> 4) + 1;  // through the word of id span (no member: zero)
+    for (int k = tm.tid; k < nw; k += tm.size) t.w[k] = 0u;
+    for (int k = tm.tid; k < tlen; k += tm.size) t.cnt[k] = 0;
+    tm.sync();
+    for (int k = tm.tid; k < tlen; k += tm.size) {
         const uint32_t r = (uint32_t)(xs[base + k] - t.lo);
         atomicOr(t.w + (r >> 4), 1u << (r & 15u));
     }
-    __syncthreads();
-    const int32_t per = ((nw + kW - 1) / kW + 31) & ~31;
+    tm.sync();
+    const int32_t per = ((nw + nwarps - 1) / nwarps + 31) & ~31;
     const int32_t w0 = min(nw, wid * per), w1 = min(nw, w0 + per);
     int tot = 0;
     for (int32_t k = w0 + lane; k < w1; k += kWarp) tot += __popc(t.w[k]);
     tot = __reduce_add_sync(0xffffffffu, tot);
     if (lane == 0) wtot[wid] = tot;
-    __syncthreads();
+    tm.sync();
     int acc = 0;
     for (int j = 0; j < wid; ++j) acc += wtot[j];
     for (int32_t k0 = w0; k0 < w1; k0 += kWarp) {
@@ -866,14 +911,78 @@ __device__ __forceinline__ void bit_build(const BitTab &t, const int32_t *__rest
         if (k < w1) t.w[k] = y | ((uint32_t)(acc + inc - c) << 16);
         acc += __shfl_sync(0xffffffffu, inc, 31);
     }
-    __syncthreads();
+    tm.sync();
 }
 
-// One CTA per item, streaming its precomputed entries. A hit c adds one to
-// (b, c) in the table, to (a, c) at the streamed slot in global memory, and
-// -- summed over the entry -- to (a, b). Dynamic shared memory: the table
-// (2^cap_logs keys, then 2^cap_logs counts; or, for a bitmap item, the
-// bitmap words, then one count per element).
+// One CTA item (owner b, a chunk of out(b), a slot range of b's row) done by
+// a team: the owner's table in `tsm` (a bitmap when the item has a dense-id
+// span, else a cuckoo hash table, rebuilt with linear probing when an
+// eviction chain runs out), its entries streamed, its counts flushed. A hit
+// c adds one to (b, c) in the table, to (a, c) at the streamed slot in global
+// memory, and -- summed over the entry -- to (a, b). Ends synchronised, so the
+// team may reuse `tsm` and `tv` for its next item.
+template <class TEAM>
+__device__ __forceinline__ void fwd_item(const TEAM &tm, const FItem &it, int *tsm, TeamVars &tv, int cap_logs,
+                                         int load_shift, const int64_t *__restrict__ foff,
+                                         const int32_t *__restrict__ fadj, const int32_t *__restrict__ fhid,
+                                         const int32_t *__restrict__ e_base, const int32_t *__restrict__ e_len,
+                                         const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt) {
+    const int32_t b = it.v;
+    const int64_t fb = foff[b];
+    const int32_t ob = (int32_t)(foff[b + 1] - fb);
+    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
+    if (tm.tid == 0) {
+        tv.next_long = 0;
+        tv.next_short = 0;
+        tv.failed = 0;
+    }
+    if (it.hspan > 0) {
+        BitTab t;
+        t.w = (uint32_t *)tsm;
+        t.lo = it.hlo;
+        t.span = (uint32_t)it.hspan;
+        t.cnt = tsm + (t.span >> 4) + 1;
+        bit_build(tm, t, fhid, fb + tb, tlen, tv.wtot);
+        ent_stream(it, t, fhid, e_base, e_len, e_fin, fcnt, &tv.next_long, &tv.next_short);
+        tm.sync();
+        ent_flush(tm, t, fhid, fb + tb, tlen, fcnt);
+        tm.sync();
+        return;
+    }
+    FTable t;
+    t.logs = min(cap_logs, max(5, fceil_log2(tlen << load_shift)));
+    t.keys = tsm;
+    t.cnt = tsm + (1 << t.logs);
+    for (int k = tm.tid; k < (1 << t.logs); k += tm.size) {
+        t.keys[k] = -1;
+        t.cnt[k] = 0;
+    }
+    tm.sync();
+    for (int k = tm.tid; k < tlen; k += tm.size)
+        if (!ck_insert(t, fadj[fb + tb + k])) tv.failed = 1;
+    tm.sync();
+    if (tv.failed) {  // an eviction chain ran out: linear probing for this table
+        for (int k = tm.tid; k < (1 << t.logs); k += tm.size) t.keys[k] = -1;
+        tm.sync();
+        for (int k = tm.tid; k < tlen; k += tm.size) lp_insert(t, fadj[fb + tb + k]);
+        tm.sync();
+        const HashTab<true> h{t};
+        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &tv.next_long, &tv.next_short);
+        tm.sync();
+        ent_flush(tm, h, fadj, fb + tb, tlen, fcnt);
+    } else {
+        const HashTab<false> h{t};
+        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &tv.next_long, &tv.next_short);
+        tm.sync();
+        ent_flush(tm, h, fadj, fb + tb, tlen, fcnt);
+    }
+    tm.sync();
+}
+
+// One CTA per item, streaming its precomputed entries (fwd_item). Dynamic
+// shared memory: the table (2^logs keys, then 2^logs counts, logs <=
+// cap_logs; or, for a bitmap item, the bitmap words, then one count per
+// element), sized for the class's largest table.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ items, const int64_t *__restrict__ foff,
                                                    const int32_t *__restrict__ fadj,
@@ -883,56 +992,70 @@ __global__ void __launch_bounds__(BLOCK) k_fwd_ent(const FItem *__restrict__ ite
                                                    const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
                                                    int cap_logs, int load_shift) {
     extern __shared__ int tsm[];
-    __shared__ int32_t next_long, next_short, failed;
-    __shared__ int32_t wtot[BLOCK / 32];
-    const FItem it = items[blockIdx.x];
-    const int32_t b = it.v;
-    const int64_t fb = foff[b];
-    const int32_t ob = (int32_t)(foff[b + 1] - fb);
-    const int32_t tb = it.chunk * kFwdChunk, te = min(tb + kFwdChunk, ob), tlen = te - tb;
-    if (threadIdx.x == 0) {
-        next_long = 0;
-        next_short = 0;
-        failed = 0;
+    __shared__ TeamVars tv;
+    const Team<BLOCK, true> tm{(int)threadIdx.x, 0};
+    fwd_item(tm, items[blockIdx.x], tsm, tv, cap_logs, load_shift, foff, fadj, fhid, e_base, e_len, e_fin, fcnt);
+}
+
+// The whole counting stage as one persistent launch: every CTA takes work
+// from one device queue until it is empty. First the CTA items of classes 2
+// and 1 (a whole 512-thread CTA per item, heaviest first), then the class-0
+// items (each quarter of the CTA, 128 threads under its own named barrier, a
+// team per item, in its quarter of the shared memory), then the warp-level
+// owners (one warp each, in its team's memory). queue[0..2] are the take
+// counters of the three parts, zero at launch; every loop is bounded by the
+// count of its part. Dynamic shared memory: max(the largest class-1/2
+// table, 4 x team_words) 32-bit words.
+constexpr int kQueueBlock = 512;
+constexpr int kQueueTeams = 4;
+constexpr int32_t kQueueMaxWords = 14336;  // 56 KB: class-2 tables above this get their own launch
+
+__global__ void __launch_bounds__(kQueueBlock, 3) k_fwd_queue(
+    const FItem *__restrict__ items2, int64_t n2, const FItem *__restrict__ items1, int64_t n1,
+    const FItem *__restrict__ items0, int64_t n0, const int32_t *__restrict__ small, int32_t nsmall,
+    unsigned long long *queue, int team_words, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+    const int32_t *__restrict__ deg, const int64_t *__restrict__ foff, const int32_t *__restrict__ fadj,
+    const int32_t *__restrict__ fhid, const uint32_t *__restrict__ fin, const int32_t *__restrict__ e_base,
+    const int32_t *__restrict__ e_len, const uint32_t *__restrict__ e_fin, int32_t *__restrict__ fcnt,
+    int rank_sorted) {
+    extern __shared__ int tsm[];
+    __shared__ TeamVars tv[kQueueTeams];
+    __shared__ int64_t pick[kQueueTeams];
+    // classes 2 and 1: the whole CTA per item
+    const Team<kQueueBlock, true> all{(int)threadIdx.x, 0};
+    for (int64_t guard = 0; guard <= n2 + n1; ++guard) {
+        if (threadIdx.x == 0) pick[0] = (int64_t)atomicAdd(queue + 0, 1ull);
+        __syncthreads();
+        const int64_t i = pick[0];
+        __syncthreads();
+        if (i >= n2 + n1) break;
+        const int cls = i < n2 ? 2 : 1;
+        fwd_item(all, i < n2 ? items2[i] : items1[i - n2], tsm, tv[0], fwd_cap_logs(cls), fwd_load_shift(cls), foff,
+                 fadj, fhid, e_base, e_len, e_fin, fcnt);
     }
-    if (it.hspan > 0) {
-        BitTab t;
-        t.w = (uint32_t *)tsm;
-        t.lo = it.hlo;
-        t.span = (uint32_t)it.hspan;
-        t.cnt = tsm + ((t.span + 15u) >> 4);
-        bit_build<BLOCK>(t, fhid, fb + tb, tlen, wtot);
-        ent_stream(it, t, fhid, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
-        __syncthreads();
-        ent_flush<BLOCK>(t, fhid, fb + tb, tlen, fcnt);
-        return;
+    // class 0: a team of 128 threads per item
+    const Team<kQueueBlock / kQueueTeams, false> tm{(int)(threadIdx.x % (kQueueBlock / kQueueTeams)),
+                                                   (int)(threadIdx.x / (kQueueBlock / kQueueTeams))};
+    int *tsm_t = tsm + (size_t)tm.id * team_words;
+    for (int64_t guard = 0; guard <= n0; ++guard) {
+        if (tm.tid == 0) pick[tm.id] = (int64_t)atomicAdd(queue + 1, 1ull);
+        tm.sync();
+        const int64_t i = pick[tm.id];
+        tm.sync();
+        if (i >= n0) break;
+        fwd_item(tm, items0[i], tsm_t, tv[tm.id], fwd_cap_logs(0), fwd_load_shift(0), foff, fadj, fhid, e_base, e_len,
+                 e_fin, fcnt);
     }
-    FTable t;
-    t.logs = min(cap_logs, max(5, fceil_log2(tlen << load_shift)));
-    t.keys = tsm;
-    t.cnt = tsm + (1 << t.logs);
-    for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) {
-        t.keys[k] = -1;
-        t.cnt[k] = 0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < tlen; k += BLOCK)
-        if (!ck_insert(t, fadj[fb + tb + k])) failed = 1;
-    __syncthreads();
-    if (failed) {  // an eviction chain ran out: linear probing for this table
-        for (int k = threadIdx.x; k < (1 << t.logs); k += BLOCK) t.keys[k] = -1;
-        __syncthreads();
-        for (int k = threadIdx.x; k < tlen; k += BLOCK) lp_insert(t, fadj[fb + tb + k]);
-        __syncthreads();
-        const HashTab<true> h{t};
-        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
-        __syncthreads();
-        ent_flush<BLOCK>(h, fadj, fb + tb, tlen, fcnt);
-    } else {
-        const HashTab<false> h{t};
-        ent_stream(it, h, fadj, e_base, e_len, e_fin, fcnt, &next_long, &next_short);
-        __syncthreads();
-        ent_flush<BLOCK>(h, fadj, fb + tb, tlen, fcnt);
+    // warp-level owners, each warp in its own part of its team's memory
+    const int lane = threadIdx.x & 31, wq = (tm.tid >> 5);
+    int *wmem = tsm_t + wq * kSmallWarpWords;
+    for (int32_t guard = 0; guard <= nsmall; ++guard) {
+        int32_t i = 0;
+        if (lane == 0) i = (int32_t)atomicAdd(queue + 2, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= nsmall) break;
+        fwd_small_owner(small[i], reinterpret_cast<unsigned long long *>(wmem), (uint32_t *)(wmem + 2 * kFwdSmallTable),
+                        wmem + 2 * kFwdSmallTable + 64, off, adj, deg, foff, fadj, fin, fcnt, rank_sorted);
     }
 }
 
@@ -1129,18 +1252,7 @@ __global__ void k_fwd_hid(const int32_t *__restrict__ fadj, int64_t m, const int
         fhid[i] = vhid[fadj[i]];
 }
 
-// CTA item classes by the owner's out-degree: 0 up to 256 (128-thread CTAs,
-// 8 KB tables), 1 up to 1024 (512 threads, 32 KB), 2 above (512 threads,
-// tables of 4096-key chunks, 128 KB)
-__host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
 
-// log2 of the hash slots of a class's tables (8 bytes per slot: 8, 32 and
-// 128 KB); a bitmap table must fit the same shared memory
-__host__ __device__ __forceinline__ int fwd_cap_logs(int cls) { return cls == 0 ? 10 : (cls == 1 ? 12 : 14); }
-
-// hash slots per key, as a shift: 2^3 in class 1 (load <= 1/8 up to 512
-// keys), 2^2 in classes 0 and 2
-__host__ __device__ __forceinline__ int fwd_load_shift(int cls) { return cls == 1 ? 3 : 2; }
 
 // warp per vertex: work as a middle vertex and the number of items
 __global__ void __launch_bounds__(256) k_fwd_sched_count(const int64_t *__restrict__ off,
@@ -1513,7 +1625,43 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
     const bool use_entries = !lean && g->fwd_entries;
     SCAN_CUDA(cudaMemsetAsync(fcnt, 0, 4 * (size_t)g->m, st));
     const int rs = g->fwd_rank_sorted ? 1 : 0;
-    if (use_entries) {
+    bool small_done = false;
+    if (use_entries && g->fwd_queue) {
+        // one persistent launch over the work queue (class-2 items whose
+        // tables do not fit its CTAs run first in their own launch)
+        const int64_t n2 = g->fwd_items_n[2], n1 = g->fwd_items_n[1], n0 = g->fwd_items_n[0];
+        auto *eb = (const int32_t *)g->fwd_ebase.ptr;
+        auto *el = (const int32_t *)g->fwd_elen.ptr;
+        auto *ef = (const uint32_t *)g->fwd_efin.ptr;
+        const int32_t team_words = std::max(n0 ? g->fwd_smem_words[0] : 0, (kQueueBlock / kQueueTeams / 32) * kSmallWarpWords);
+        const bool sep2 = n2 > 0 && g->fwd_smem_words[2] > kQueueMaxWords;
+        int32_t words = kQueueTeams * team_words;
+        if (n1) words = std::max(words, g->fwd_smem_words[1]);
+        if (n2 && !sep2) words = std::max(words, g->fwd_smem_words[2]);
+        if (sep2) {
+            const size_t smem = 4 * (size_t)g->fwd_smem_words[2];
+            SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_fwd_ent<512><<<(unsigned)n2, 512, smem, st>>>((const FItem *)g->fwd_items[2].ptr, foff, fadj, fhid, eb, el,
+                                                            ef, fcnt, fwd_cap_logs(2), fwd_load_shift(2));
+            c->launches++;
+        }
+        if (!g->fwd_qctr.ptr) SCAN_TRY(dev_alloc(c, g->fwd_qctr, 4 * sizeof(unsigned long long)));
+        SCAN_CUDA(cudaMemsetAsync(g->fwd_qctr.ptr, 0, 4 * sizeof(unsigned long long), st));
+        const size_t smem = 4 * (size_t)words;
+        SCAN_CUDA(cudaFuncSetAttribute(k_fwd_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SCAN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_queue, kQueueBlock, smem));
+        const int64_t work = (sep2 ? 0 : n2) + n1 + (n0 + kQueueTeams - 1) / kQueueTeams +
+                             (g->fwd_small + kQueueBlock / 32 - 1) / (kQueueBlock / 32);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * c->num_sms, work));
+        k_fwd_queue<<<grid, kQueueBlock, smem, st>>>(
+            (const FItem *)g->fwd_items[2].ptr, sep2 ? 0 : n2, (const FItem *)g->fwd_items[1].ptr, n1,
+            (const FItem *)g->fwd_items[0].ptr, n0, (const int32_t *)g->fwd_owners.ptr, g->fwd_small,
+            (unsigned long long *)g->fwd_qctr.ptr, team_words, off, adj, deg, foff, fadj, fhid, fin, eb, el, ef, fcnt,
+            rs);
+        c->launches++;
+        small_done = true;
+    } else if (use_entries) {
         for (int cls = 2; cls >= 0; --cls) {
             const int64_t ni = g->fwd_items_n[cls];
             if (ni == 0) continue;
@@ -1554,7 +1702,7 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
                                                              foff, fadj, fin, fcnt, cap_lognb, load_shift, rs);
         c->launches++;
     }
-    if (g->fwd_small > 0) {
+    if (g->fwd_small > 0 && !small_done) {
         k_fwd_small<<<grid_for((int64_t)g->fwd_small * kWarp, 256, c->num_sms * 16), 256, 0, st>>>(
             (const int32_t *)g->fwd_owners.ptr, g->fwd_small, off, adj, deg, foff, fadj, fin, fcnt, rs);
         c->launches++;

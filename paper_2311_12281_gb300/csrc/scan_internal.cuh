@@ -77,6 +77,8 @@ struct Graph {
     bool fwd_entries_tried = false;        // a build was attempted (it is skipped when it does not fit)
     bool fwd_rank_sorted = false;  // out-lists ordered by (deg, id) instead of id
     int32_t fwd_smem_words[3] = {0, 0, 0};  // shared memory the largest table of each item class needs
+    bool fwd_queue = false;  // count in one persistent launch over a work queue (else one launch per class)
+    DevBuf fwd_qctr;        // its take counters
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
@@ -112,7 +114,7 @@ struct Graph {
     template <class F>
     void for_each_buf(F f) {
         DevBuf *bufs[] = {&off, &adj, &src, &rev, &deg, &oe, &cn_cache, &cdd, &owners_small, &items[0], &items[1],
-                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fhid, &fwd_owners,
+                          &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fhid, &fwd_qctr, &fwd_owners,
                           &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
                           &qparams, &sim, &simo, &nsim, &hst, &mslots, &core, &cid, &parent, &label,
                           &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
