@@ -97,6 +97,19 @@ SCAN_API scan_status scan_ctx_profile(scan_ctx *ctx, int32_t enable);
 /* Synchronises, then returns the summed milliseconds and number of timed
  * intervals of a stage since profiling was (re)enabled. */
 SCAN_API scan_status scan_ctx_stage_time(scan_ctx *ctx, int32_t stage, double *total_ms, int64_t *intervals);
+/*
+ * Iteration cap of the union-find loops (Algorithm 3's root walks and hook
+ * retries; every device loop of this library is bounded) for the context's
+ * later queries, resident and out of core: limit = 0 restores the compiled
+ * bound (2^22 iterations, never reached by a correct run); a smaller value
+ * lowers it. A query whose loops run out returns SCAN_ETIMEOUT with no
+ * result; the context and its graphs stay usable. This exists to exercise
+ * that error path (a diagnostic: limits far below a graph's union-find
+ * depth make queries fail). While a cap is set, queries run their kernels
+ * directly instead of replaying a captured CUDA graph. Synchronises the
+ * context's stream first.
+ */
+SCAN_API scan_status scan_ctx_set_loop_limit(scan_ctx *ctx, uint32_t limit);
 
 /* ---------------------------------------------------------------- graph */
 /* Load flags. */
@@ -145,6 +158,10 @@ SCAN_API scan_status scan_graph_load_partitioned(scan_ctx *ctx, int32_t n, const
                                                  scan_graph **out);
 /* Number of row blocks of a partitioned graph (0 for a resident one). */
 SCAN_API int32_t scan_graph_blocks(const scan_graph *g);
+/* Host-to-device bytes a partitioned graph's blocks have been copied in, in
+ * total since it was loaded (validation and every query; Section 5's
+ * transfer volume); 0 for a resident graph. */
+SCAN_API uint64_t scan_graph_transfer_bytes(const scan_graph *g);
 SCAN_API int32_t scan_graph_n(const scan_graph *g);
 SCAN_API int64_t scan_graph_nnz(const scan_graph *g);
 /* Device bytes held by this graph (including its count cache). */
@@ -179,6 +196,13 @@ typedef struct scan_params {
 #define SCAN_STRATEGY_FORWARD_LEAN 3 /* FORWARD without its precomputed per-item entry lists (12 bytes
                                         per oriented edge): derived round by round, slower; FORWARD
                                         falls back to it when the lists do not fit the budget */
+#define SCAN_STRATEGY_PROGRESSIVE 4 /* per edge, BSEARCH's intersection with the paper's progressive
+                                       role-based skipping (Algorithms 2-3): an edge whose two endpoints'
+                                       core roles the bounds already fix is not intersected during core
+                                       detection; afterwards only core-core edges not yet in one
+                                       union-find tree and core-non-core edges are; non-core pairs never.
+                                       Queries only (no count cache): SCAN_Q_BUILD_CACHE counts with
+                                       BSEARCH */
 /* Select the similarity kernel family used by SCAN_Q_RECOMPUTE and
  * SCAN_Q_BUILD_CACHE on this graph (SCAN_Q_PLAIN always uses BSEARCH without
  * pruning). SCAN_EINVAL for an unknown value. */
@@ -295,7 +319,9 @@ SCAN_API scan_status scan_query_batch(scan_graph *const *gs, const scan_params *
 typedef struct scan_server scan_server;
 typedef struct scan_server_opts {
     int32_t max_inflight; /* concurrent requests on the device, 1..256 */
-    int32_t use_cache;    /* 1: keep per-edge counts after a graph's first query; 0: recompute every query */
+    int32_t use_cache;    /* 1: keep per-edge counts after a graph's first query; 0: recompute every query
+                             with the graph's kernel family; 2: every query by the plain comparator path
+                             (SCAN_Q_PLAIN: binary-search counts of every edge, no pruning, no cache) */
 } scan_server_opts;
 typedef struct scan_server_report {
     uint64_t completed, rejected;
@@ -346,11 +372,14 @@ SCAN_API void scan_server_destroy(scan_server *srv);
  * Working memory is one fixed 64 MiB __device__ array inside the library
  * (held by every GPU that loads it until the process exits): graphs need
  * 4(n+1) + 8 nnz bytes plus alignment of it, about n + 2 nnz <= 16.7M
- * entries; larger graphs get SCAN_EINVAL before any device work. The first
- * call on a device looks up that array's device address (once per device);
- * make that first call before any stream capture. All calls share the one
- * array and it keeps the last call's contents, so calls that overlap on the
- * GPU (other threads, other streams) race: serialise them.
+ * entries; larger graphs get SCAN_EINVAL before any device work. Every call
+ * looks up that array's device address on the current device (no state is
+ * cached across calls, so a device reset leaves nothing stale). The call
+ * synchronises `stream` and copies an error word to the host, so it must
+ * never be called while that stream is being captured into a CUDA graph.
+ * The array lies outside any context's budget_bytes accounting. All calls
+ * share the one array and it keeps the last call's contents, so calls that
+ * overlap on the GPU (other threads, other streams) race: serialise them.
  */
 SCAN_API scan_status scan_common_counts_static(const int64_t *offsets, const int32_t *adj, int32_t n, int64_t nnz,
                                                int32_t *cn, void *stream);

@@ -73,12 +73,14 @@ SIGNATURES = {
     "scan_ctx_kernel_launches": (_U64, [_VP]),
     "scan_ctx_sync": (ctypes.c_int, [_VP]),
     "scan_ctx_profile": (ctypes.c_int, [_VP, _I32]),
+    "scan_ctx_set_loop_limit": (ctypes.c_int, [_VP, ctypes.c_uint32]),
     "scan_ctx_stage_time": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]),
     "scan_graph_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _U32, _PP]),
     "scan_graph_free": (None, [_VP]),
     "scan_graph_load_partitioned": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _I64, _PP]),
     "scan_graph_blocks": (_I32, [_VP]),
+    "scan_graph_transfer_bytes": (_U64, [_VP]),
     "scan_graph_n": (_I32, [_VP]),
     "scan_graph_nnz": (_I64, [_VP]),
     "scan_graph_device_bytes": (_U64, [_VP]),
@@ -177,6 +179,10 @@ def scan_ctx_profile(ctx: int, enable: bool):
     _check(lib().scan_ctx_profile(ctx, 1 if enable else 0))
 
 
+def scan_ctx_set_loop_limit(ctx: int, limit: int):
+    _check(lib().scan_ctx_set_loop_limit(ctx, ctypes.c_uint32(int(limit))))
+
+
 def scan_ctx_stage_time(ctx: int, stage: int) -> tuple[float, int]:
     """(summed milliseconds, number of timed intervals) of one stage."""
     ms = ctypes.c_double()
@@ -222,6 +228,10 @@ def scan_graph_blocks(g: int) -> int:
     return int(lib().scan_graph_blocks(g))
 
 
+def scan_graph_transfer_bytes(g: int) -> int:
+    return int(lib().scan_graph_transfer_bytes(g))
+
+
 def scan_graph_n(g: int) -> int:
     return int(lib().scan_graph_n(g))
 
@@ -243,6 +253,7 @@ def scan_graph_has_cache(g: int) -> bool:
 
 
 SCAN_STRATEGY_FORWARD, SCAN_STRATEGY_OWNER, SCAN_STRATEGY_BSEARCH, SCAN_STRATEGY_FORWARD_LEAN = 0, 1, 2, 3
+SCAN_STRATEGY_PROGRESSIVE = 4
 
 
 def scan_graph_set_strategy(g: int, strategy: int):
@@ -393,9 +404,10 @@ def scan_common_counts_static(offsets: int, adj: int, n: int, nnz: int, cn: int,
     _check(lib().scan_common_counts_static(offsets, adj, int(n), int(nnz), cn, stream))
 
 
-def scan_server_create(ctx: int, max_inflight: int = 8, use_cache: bool = True) -> int:
+def scan_server_create(ctx: int, max_inflight: int = 8, use_cache: bool | int = True) -> int:
+    """use_cache: True/1 cached counts, False/0 recompute every query, 2 the plain comparator path."""
     out = ctypes.c_void_p()
-    opts = scan_server_opts(int(max_inflight), 1 if use_cache else 0)
+    opts = scan_server_opts(int(max_inflight), int(use_cache))
     _check(lib().scan_server_create(ctx, ctypes.byref(opts), ctypes.byref(out)))
     return out.value
 
@@ -530,6 +542,10 @@ class Graph:
     @property
     def blocks(self) -> int:
         return scan_graph_blocks(self.handle)
+
+    @property
+    def transfer_bytes(self) -> int:
+        return scan_graph_transfer_bytes(self.handle)
 
     def free(self):
         if self.handle:

@@ -185,6 +185,14 @@ scan_status scan_ctx_profile(scan_ctx *c, int32_t enable) {
     return SCAN_OK;
 }
 
+scan_status scan_ctx_set_loop_limit(scan_ctx *c, uint32_t limit) {
+    if (!c) { set_error("ctx is NULL"); return SCAN_EINVAL; }
+    SCAN_CUDA(cudaSetDevice(c->device));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));  // queries already queued keep the cap they were launched with
+    c->loop_limit = limit;
+    return SCAN_OK;
+}
+
 scan_status scan_ctx_stage_time(scan_ctx *c, int32_t stage, double *total_ms, int64_t *intervals) {
     if (!c || !total_ms || stage < 0 || stage >= SCAN_STAGE_COUNT) { set_error("bad arguments"); return SCAN_EINVAL; }
     SCAN_CUDA(cudaSetDevice(c->device));
@@ -415,6 +423,8 @@ int32_t scan_graph_blocks(const scan_graph *g) {
     return g && g->part ? part_block_count(g) : 0;
 }
 
+uint64_t scan_graph_transfer_bytes(const scan_graph *g) { return g && g->part ? part_transfer_bytes(g) : 0; }
+
 void scan_graph_free(scan_graph *g) { graph_destroy(g); }
 
 int32_t scan_graph_n(const scan_graph *g) { return g ? g->n : 0; }
@@ -442,7 +452,7 @@ scan_status scan_graph_set_strategy(scan_graph *g, int32_t strategy) {
     if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
     if (g->part) { set_error("not available for a partitioned graph"); return SCAN_EINVAL; }
     if (strategy != SCAN_STRATEGY_FORWARD && strategy != SCAN_STRATEGY_OWNER && strategy != SCAN_STRATEGY_BSEARCH &&
-        strategy != SCAN_STRATEGY_FORWARD_LEAN) {
+        strategy != SCAN_STRATEGY_FORWARD_LEAN && strategy != SCAN_STRATEGY_PROGRESSIVE) {
         set_error("unknown strategy " + std::to_string(strategy));
         return SCAN_EINVAL;
     }

@@ -209,8 +209,8 @@ __device__ __forceinline__ void for_each_similar(const uint8_t *__restrict__ sim
 }
 
 // ------------------------------------------------------------------ union-find
-__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t *err) {
-    for (int it = 0; it < kUfLimit; ++it) {
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t *err, int limit) {
+    for (int it = 0; it < limit; ++it) {
         int32_t p = ((volatile int32_t *)parent)[x];
         if (p == x) return x;
         int32_t gp = ((volatile int32_t *)parent)[p];
@@ -222,10 +222,10 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t 
 }
 
 // Hook the larger root under the smaller one (CAS on the root's own entry).
-__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *err) {
-    for (int it = 0; it < kUfLimit; ++it) {
-        a = uf_find(parent, a, err);
-        b = uf_find(parent, b, err);
+__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *err, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        a = uf_find(parent, a, err, limit);
+        b = uf_find(parent, b, err, limit);
         if (a == b) return;
         if (a > b) { int32_t t = a; a = b; b = t; }
         int32_t old = atomicCAS(parent + b, b, a);
@@ -239,20 +239,199 @@ __global__ void __launch_bounds__(kBlock) k_uf_hook(const int32_t *__restrict__ 
                                                    const uint32_t *__restrict__ oe, int64_t m,
                                                    const uint8_t *__restrict__ simo,
                                                    const uint8_t *__restrict__ core, int32_t *parent,
-                                                   uint32_t *err) {
+                                                   uint32_t *err, int limit) {
     for_each_similar(simo, m, [&](int64_t i) {
         const uint32_t e = oe[i];
         const int32_t u = src[e], v = adj[e];
-        if (core[u] && core[v]) uf_unite(parent, u, v, err);
+        if (core[u] && core[v]) uf_unite(parent, u, v, err, limit);
     });
 }
 
 __global__ void k_uf_final(const uint8_t *__restrict__ core, int32_t n, int32_t *parent, int32_t *__restrict__ cid,
-                           uint32_t *err) {
+                           uint32_t *err, int limit) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
-    cid[u] = core[u] ? uf_find(parent, (int32_t)u, err) : -1;
+    cid[u] = core[u] ? uf_find(parent, (int32_t)u, err, limit) : -1;
 }
+
+// ------------------------------------------------------------------ progressive skipping
+// The paper's progressive, role-based skipping (Algorithm 2's bounds,
+// Algorithm 3's same-tree test) on the per-edge family. Per oriented edge a
+// state: 0 not yet decided, 1 eps-similar, 2 not. Per vertex the bounds of
+// |N_eps[u]| - 1: lb[u] = similar neighbours found so far (the ordinary
+// eps-degree array) and ub[u] = neighbours not yet found dissimilar. u's
+// role is fixed once 1 + lb[u] >= mu (core) or 1 + ub[u] < mu (not); both
+// only tighten, so a role read as fixed stays fixed. An edge whose two
+// endpoints' roles are fixed is not intersected while cores are found; a
+// vertex whose role is still open at the end has had every edge decided, so
+// 1 + lb[u] >= mu is its exact core test and the ordinary core kernel reads
+// lb as its eps-degree. After it, only core-core edges between different
+// union-find trees and core-non-core edges still need their similarity.
+
+// exact closed count of the edge (u, v), the smaller row probed in the larger
+// (the whole warp), and the eps-test
+__device__ __forceinline__ bool warp_eps_edge(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                              int32_t u, int32_t v, int32_t du, int32_t dv, uint64_t pp,
+                                              uint64_t qq) {
+    const int lane = threadIdx.x & 31;
+    if (dev::prune_dissimilar((uint64_t)min(du, dv) + 1, (uint64_t)max(du, dv) + 1, pp, qq)) return false;
+    if (dev::prune_similar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) return true;
+    const int32_t a = du <= dv ? u : v, b = du <= dv ? v : u;
+    const int32_t da = min(du, dv), db = max(du, dv);
+    const int32_t *ra = adj + off[a];
+    const int32_t *rb = adj + off[b];
+    int c = 0;
+    for (int32_t k = lane; k < da; k += kWarp) c += contains(rb, db, __ldg(ra + k));
+    c = __reduce_add_sync(0xffffffffu, c) + 2;
+    return dev::eps_similar((uint64_t)c, (uint64_t)du + 1, (uint64_t)dv + 1, pp, qq);
+}
+
+__device__ __forceinline__ bool role_fixed(const int32_t *lb, const int32_t *ub, int32_t u, uint32_t mu) {
+    const uint32_t l = (uint32_t)((volatile const int32_t *)lb)[u], h = (uint32_t)((volatile const int32_t *)ub)[u];
+    return l + 1u >= mu || h + 1u < mu;
+}
+
+// Degree-only outcomes first (A1's prune, thread per oriented edge): they
+// cost no intersection and tighten the bounds before any is made.
+__global__ void __launch_bounds__(kBlock) k_prog_degree(const int32_t *__restrict__ adj,
+                                                       const int32_t *__restrict__ src,
+                                                       const int32_t *__restrict__ deg,
+                                                       const uint32_t *__restrict__ oe, int64_t m, QParams qp,
+                                                       uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
+                                                       int32_t *lb, int32_t *ub) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) {
+        const uint32_t e = oe[i];
+        const int32_t u = src[e], v = adj[e];
+        const uint64_t du1 = (uint64_t)deg[u] + 1, dv1 = (uint64_t)deg[v] + 1;
+        uint64_t pp, qq;
+        qp.eps(u, pp, qq);
+        if (dev::prune_dissimilar(du1 < dv1 ? du1 : dv1, du1 < dv1 ? dv1 : du1, pp, qq)) {
+            state[i] = 2;
+            atomicSub(ub + u, 1);
+            atomicSub(ub + v, 1);
+        } else if (dev::prune_similar(du1, dv1, pp, qq)) {
+            state[i] = 1;
+            simo[i] = 1;
+            atomicAdd(lb + u, 1);
+            atomicAdd(lb + v, 1);
+        }
+    }
+}
+
+// The warps of these kernels screen 32 edges at a time, lane l on edge
+// (32 t + l) W + w for warp w of W (so the heavy edges of one row spread over
+// all warps), then intersect the edges that need it one after another.
+#define PROG_EDGES_BEGIN                                                                              \
+    const int lane = threadIdx.x & 31;                                                                \
+    const int64_t W = (int64_t)gridDim.x * (kBlock / kWarp);                                          \
+    const int64_t w = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kWarp;                           \
+    for (int64_t k0 = 0; k0 * W + w < m; k0 += kWarp) {                                               \
+        const int64_t i = (k0 + lane) * W + w;
+
+// Core detection with skipping: an edge is intersected unless both its
+// endpoints' roles are already fixed.
+__global__ void __launch_bounds__(kBlock) k_prog_core(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                     const int32_t *__restrict__ src, const int32_t *__restrict__ deg,
+                                                     const uint32_t *__restrict__ oe, int64_t m, QParams qp,
+                                                     uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
+                                                     int32_t *lb, int32_t *ub) {
+    PROG_EDGES_BEGIN
+        int32_t u = 0, v = 0;
+        bool need = false;
+        if (i < m && state[i] == 0) {
+            const uint32_t e = oe[i];
+            u = src[e];
+            v = adj[e];
+            const uint32_t mu = qp.mu_of(u);
+            need = !(role_fixed(lb, ub, u, mu) && role_fixed(lb, ub, v, mu));
+        }
+        for (unsigned todo = __ballot_sync(0xffffffffu, need); todo; todo &= todo - 1) {
+            const int j = __ffs(todo) - 1;
+            const int32_t uj = __shfl_sync(0xffffffffu, u, j), vj = __shfl_sync(0xffffffffu, v, j);
+            const int64_t ij = (k0 + j) * W + w;
+            uint64_t pp, qq;
+            qp.eps(uj, pp, qq);
+            const bool s = warp_eps_edge(off, adj, uj, vj, deg[uj], deg[vj], pp, qq);
+            if (lane == 0) {
+                state[ij] = s ? 1 : 2;
+                simo[ij] = s ? 1 : 0;
+                if (s) {
+                    atomicAdd(lb + uj, 1);
+                    atomicAdd(lb + vj, 1);
+                } else {
+                    atomicSub(ub + uj, 1);
+                    atomicSub(ub + vj, 1);
+                }
+            }
+        }
+    }
+}
+
+// Clusters with skipping: after the decided similar core-core edges are
+// hooked, each still undecided core-core edge whose endpoints have different
+// roots is intersected, and hooked when similar.
+__global__ void __launch_bounds__(kBlock) k_prog_union(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                      const int32_t *__restrict__ src, const int32_t *__restrict__ deg,
+                                                      const uint32_t *__restrict__ oe, int64_t m, QParams qp,
+                                                      uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
+                                                      const uint8_t *__restrict__ core, int32_t *parent, uint32_t *err,
+                                                      int limit) {
+    PROG_EDGES_BEGIN
+        int32_t u = 0, v = 0;
+        bool need = false;
+        if (i < m && state[i] == 0) {
+            const uint32_t e = oe[i];
+            u = src[e];
+            v = adj[e];
+            need = core[u] && core[v];
+        }
+        for (unsigned todo = __ballot_sync(0xffffffffu, need); todo; todo &= todo - 1) {
+            const int j = __ffs(todo) - 1;
+            const int32_t uj = __shfl_sync(0xffffffffu, u, j), vj = __shfl_sync(0xffffffffu, v, j);
+            const int64_t ij = (k0 + j) * W + w;
+            int same = 0;
+            if (lane == 0) same = uf_find(parent, uj, err, limit) == uf_find(parent, vj, err, limit);
+            if (__shfl_sync(0xffffffffu, same, 0)) continue;  // one tree already: the edge changes nothing
+            uint64_t pp, qq;
+            qp.eps(uj, pp, qq);
+            const bool s = warp_eps_edge(off, adj, uj, vj, deg[uj], deg[vj], pp, qq);
+            if (lane == 0) {
+                state[ij] = s ? 1 : 2;
+                if (s) {
+                    simo[ij] = 1;
+                    uf_unite(parent, uj, vj, err, limit);
+                }
+            }
+        }
+    }
+}
+
+// Borders: every still undecided edge with exactly one core endpoint.
+__global__ void __launch_bounds__(kBlock) k_prog_border(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                       const int32_t *__restrict__ src, const int32_t *__restrict__ deg,
+                                                       const uint32_t *__restrict__ oe, int64_t m, QParams qp,
+                                                       const uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
+                                                       const uint8_t *__restrict__ core) {
+    PROG_EDGES_BEGIN
+        int32_t u = 0, v = 0;
+        bool need = false;
+        if (i < m && state[i] == 0) {
+            const uint32_t e = oe[i];
+            u = src[e];
+            v = adj[e];
+            need = core[u] != core[v];
+        }
+        for (unsigned todo = __ballot_sync(0xffffffffu, need); todo; todo &= todo - 1) {
+            const int j = __ffs(todo) - 1;
+            const int32_t uj = __shfl_sync(0xffffffffu, u, j), vj = __shfl_sync(0xffffffffu, v, j);
+            uint64_t pp, qq;
+            qp.eps(uj, pp, qq);
+            const bool s = warp_eps_edge(off, adj, uj, vj, deg[uj], deg[vj], pp, qq);
+            if (lane == 0 && s) simo[(k0 + j) * W + w] = 1;
+        }
+    }
+}
+#undef PROG_EDGES_BEGIN
 
 // ------------------------------------------------------------------ borders
 // Membership code memb[v] (the parent array after union-find): a core's cid;
@@ -639,7 +818,8 @@ scan_status build_count_cache(Graph *g) {
     SCAN_TRY(cache_reserve(g));
     int32_t *cn = (int32_t *)g->cn_cache.ptr;
     uint64_t *dd = (uint64_t *)g->cdd.ptr;
-    if (g->strategy == SCAN_STRATEGY_OWNER || g->strategy == SCAN_STRATEGY_BSEARCH) {
+    if (g->strategy == SCAN_STRATEGY_OWNER || g->strategy == SCAN_STRATEGY_BSEARCH ||
+        g->strategy == SCAN_STRATEGY_PROGRESSIVE) {
         // per-slot counts into the border scratch (free outside a query's border stage), then oriented
         int32_t *slot_cn = (int32_t *)g->raw.ptr;
         if (g->strategy == SCAN_STRATEGY_OWNER) SCAN_TRY(launch_owner_isect(g, false, false, true, QParams{}, slot_cn));
@@ -683,6 +863,7 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     auto *err = (uint32_t *)g->err.ptr;
     const unsigned gm = grid_for(m, kBlock, c->num_sms * 32);
     const unsigned gs = grid_for((m + 15) / 16, kBlock, c->num_sms * 32);  // 16 flags per thread
+    bool progressive = false;  // the similarity stage left undecided edges (progressive skipping)
 
     {
         StageTimer t(c, SCAN_STAGE_SIMILARITY);
@@ -693,6 +874,23 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
             if (m > 0) {
                 k_sim_from_counts<<<gm, kBlock, 0, st>>>(adj, src, oe, m, (const int32_t *)g->cn_cache.ptr,
                                                          (const uint64_t *)g->cdd.ptr, qp, simo, nsim);
+                c->launches++;
+            }
+        } else if (!(mode & SCAN_Q_PLAIN) && g->strategy == SCAN_STRATEGY_PROGRESSIVE) {
+            // core detection with skipping: simo and the lower bounds (nsim)
+            // from the decided edges; the upper bounds start at the degrees
+            progressive = true;
+            if (!g->sim.ptr) SCAN_TRY(dev_alloc(c, g->sim, (size_t)(nnz > 0 ? nnz : 1)));
+            if (m > 0) {
+                SCAN_CUDA(cudaMemsetAsync(g->sim.ptr, 0, (size_t)m, st));
+                SCAN_CUDA(cudaMemsetAsync(simo, 0, (size_t)m, st));
+                SCAN_CUDA(cudaMemcpyAsync(g->hst.ptr, g->deg.ptr, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+                k_prog_degree<<<gm, kBlock, 0, st>>>(adj, src, (const int32_t *)g->deg.ptr, oe, m, qp,
+                                                     (uint8_t *)g->sim.ptr, simo, nsim, (int32_t *)g->hst.ptr);
+                c->launches++;
+                k_prog_core<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
+                    off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, nsim,
+                    (int32_t *)g->hst.ptr);
                 c->launches++;
             }
         } else if (!(mode & SCAN_Q_PLAIN) && g->strategy != SCAN_STRATEGY_OWNER &&
@@ -733,9 +931,22 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
     }
     {
         StageTimer t(c, SCAN_STAGE_CLUSTER);
-        if (m > 0) k_uf_hook<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, parent, err);
-        k_uf_final<<<gt, kBlock, 0, st>>>(core, n, parent, cid, err);
+        const int uf_limit = c->loop_limit ? (int)std::min<uint32_t>(c->loop_limit, kUfLimit) : kUfLimit;
+        if (m > 0) k_uf_hook<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, parent, err, uf_limit);
+        if (m > 0 && progressive) {
+            k_prog_union<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
+                off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, core, parent, err,
+                uf_limit);
+            c->launches++;
+        }
+        k_uf_final<<<gt, kBlock, 0, st>>>(core, n, parent, cid, err, uf_limit);
         c->launches += 1 + (m > 0);
+    }
+    if (m > 0 && progressive) {  // the borders' similarities not decided yet
+        StageTimer t(c, SCAN_STAGE_BORDER);
+        k_prog_border<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
+            off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (const uint8_t *)g->sim.ptr, simo, core);
+        c->launches++;
     }
     int64_t *cnt_off = (int64_t *)g->cnt_off.ptr;
     int32_t *ucnt = (int32_t *)g->ucnt.ptr;
@@ -813,7 +1024,8 @@ scan_status query_replay(Graph *g, const scan_params &p, uint32_t mode, uint8_t 
                          int32_t *pairs, int64_t pairs_cap, int64_t *npairs) {
     Ctx *c = g->ctx;
     // building a cache, profiling, or a graph without the buffers: run directly
-    if ((mode & SCAN_Q_BUILD_CACHE) || c->profiling || g->qgraph_off || g->part)
+    // (and with a test cap on the union-find loops: replays keep the compiled bound)
+    if ((mode & SCAN_Q_BUILD_CACHE) || c->profiling || g->qgraph_off || g->part || c->loop_limit)
         return query_pipeline(g, uniform_params(p), mode, core, cid, label, pairs, pairs_cap, npairs);
     if (!g->qparams.ptr) SCAN_TRY(dev_alloc(c, g->qparams, 3 * sizeof(uint64_t)));
     if (!g->h_qparams) SCAN_CUDA(cudaMallocHost(&g->h_qparams, 3 * sizeof(uint64_t)));
