@@ -40,6 +40,7 @@ struct Part {
     bool pending[3] = {false, false, false};  // copied on the side stream; compute has not waited yet
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copied[3] = {nullptr, nullptr, nullptr};
+    uint64_t h2d_bytes = 0;  // block copies issued since the load
 };
 
 namespace {
@@ -206,8 +207,8 @@ __global__ void k_p_core(const int32_t *__restrict__ ecnt, int32_t n, uint32_t m
 }
 
 // ------------------------------------------------------------ pass 2
-__device__ int32_t p_find(int32_t *parent, int32_t x, uint32_t *err) {
-    for (int it = 0; it < kUfLimitP; ++it) {
+__device__ int32_t p_find(int32_t *parent, int32_t x, uint32_t *err, int limit) {
+    for (int it = 0; it < limit; ++it) {
         const int32_t p = ((volatile int32_t *)parent)[x];
         if (p == x) return x;
         const int32_t gp = ((volatile int32_t *)parent)[p];
@@ -218,10 +219,10 @@ __device__ int32_t p_find(int32_t *parent, int32_t x, uint32_t *err) {
     return x;
 }
 
-__device__ void p_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *err) {
-    for (int it = 0; it < kUfLimitP; ++it) {
-        a = p_find(parent, a, err);
-        b = p_find(parent, b, err);
+__device__ void p_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *err, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        a = p_find(parent, a, err, limit);
+        b = p_find(parent, b, err, limit);
         if (a == b) return;
         if (a > b) { const int32_t t = a; a = b; b = t; }
         if (atomicCAS(parent + b, b, a) == b) return;
@@ -232,7 +233,7 @@ __device__ void p_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *err) {
 // warp per row of the block: core-core similar edges with v > u join
 __global__ void k_p_hook(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int32_t v0, int32_t rows,
                          int64_t e0, const uint32_t *__restrict__ bits, const uint8_t *__restrict__ core,
-                         int32_t *parent, uint32_t *err) {
+                         int32_t *parent, uint32_t *err, int limit) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
@@ -240,7 +241,7 @@ __global__ void k_p_hook(const int64_t *__restrict__ off, const int32_t *__restr
     if (!core[u]) return;
     for (int64_t s = off[r] + lane; s < off[r + 1]; s += 32) {
         const int32_t v = adj[s - e0];
-        if (v > u && sbit(bits, s) && core[v]) p_unite(parent, u, v, err);
+        if (v > u && sbit(bits, s) && core[v]) p_unite(parent, u, v, err, limit);
     }
 }
 
@@ -248,10 +249,10 @@ __global__ void k_p_hook(const int64_t *__restrict__ off, const int32_t *__restr
 // path halving of concurrent finds (which may store a non-root ancestor over
 // a root written a moment earlier)
 __global__ void k_p_final(const uint8_t *__restrict__ core, int32_t n, int32_t *parent, int32_t *__restrict__ cid,
-                          uint32_t *err) {
+                          uint32_t *err, int limit) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    cid[v] = core[v] ? p_find(parent, (int32_t)v, err) : -1;
+    cid[v] = core[v] ? p_find(parent, (int32_t)v, err, limit) : -1;
 }
 
 // ------------------------------------------------------------ pass 3
@@ -379,6 +380,7 @@ static scan_status load_block(Graph *g, int slot, int bi, bool async) {
     if (B.e1 > B.e0)
         SCAN_CUDA(cudaMemcpyAsync(P->badj[slot].ptr, P->h_adj + B.e0, 4 * (size_t)(B.e1 - B.e0),
                                   cudaMemcpyHostToDevice, st));
+    P->h2d_bytes += 8 * ((uint64_t)rows + 1) + 4 * (uint64_t)(B.e1 - B.e0);
     SCAN_CUDA(cudaEventRecord(P->copied[slot], st));
     P->loaded[slot] = bi;
     P->pending[slot] = async;
@@ -403,6 +405,8 @@ static scan_status release_slot(Graph *g, int slot) {
 }
 
 int32_t part_block_count(const Graph *g) { return g->part ? (int32_t)g->part->blocks.size() : 0; }
+
+uint64_t part_transfer_bytes(const Graph *g) { return g->part ? g->part->h2d_bytes : 0; }
 
 void part_release(Graph *g) {
     Part *P = g->part;
@@ -481,23 +485,48 @@ scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32
     if (s == SCAN_OK) s = dev_alloc(ctx, P->err, 16);
     if (s == SCAN_OK) s = dev_alloc(ctx, g->label, N1);
     if (s != SCAN_OK) return fail(s);
-    // blocks: what is left of the budget, for three block slots plus per-block scratch
-    uint64_t avail = ctx->budget ? (ctx->budget > ctx->used ? ctx->budget - ctx->used : 0) : (uint64_t)4 << 30;
-    int64_t cap_slots = block_slots_hint > 0 ? block_slots_hint : (int64_t)(avail / 5 / 12);
-    // a block holds rows up to cap_slots slots; a longer row forms a block alone
-    cap_slots = std::max<int64_t>(cap_slots, 1);
-    for (int32_t v = 0; v < n;) {
-        Block B;
-        B.v0 = v;
-        B.e0 = offsets[v];
-        int32_t w = v;
-        while (w < n && (offsets[w + 1] - B.e0 <= cap_slots || w == v)) ++w;
-        B.v1 = w;
-        B.e1 = offsets[w];
-        P->blocks.push_back(B);
-        P->max_rows = std::max(P->max_rows, B.v1 - B.v0);
-        P->max_slots = std::max(P->max_slots, B.e1 - B.e0);
-        v = w;
+    // Blocks from what is left of the budget. The block-sized device memory
+    // is three block slots (8 B per row offset, 4 B per slot), the per-row
+    // scratch (24 B), the pass-1 chunks (12 B per row and per slot) and the
+    // border candidates and pairs of pass 3 (12 B per slot): 60 B per row and
+    // 36 B per slot of the largest block. Rows go into a block while it stays
+    // within 90 % of that; the plan shrinks until the largest block's rows
+    // and slots together fit (a single row longer than that forms a block
+    // alone, and its load fails with SCAN_EBUDGET if it cannot fit at all).
+    const uint64_t avail = ctx->budget ? (ctx->budget > ctx->used ? ctx->budget - ctx->used : 0)
+                                       : (uint64_t)4 << 30;
+    auto plan = [&](double cap_bytes, int64_t cap_slots) {
+        P->blocks.clear();
+        P->max_rows = 0;
+        P->max_slots = 0;
+        for (int32_t v = 0; v < n;) {
+            Block B;
+            B.v0 = v;
+            B.e0 = offsets[v];
+            int32_t w = v;
+            while (w < n) {
+                const int64_t rows = (int64_t)w + 1 - v, slots = offsets[w + 1] - B.e0;
+                const bool fits = cap_slots > 0 ? slots <= cap_slots : 60.0 * rows + 36.0 * slots <= cap_bytes;
+                if (!fits && w > v) break;
+                ++w;
+            }
+            B.v1 = w;
+            B.e1 = offsets[w];
+            P->blocks.push_back(B);
+            P->max_rows = std::max(P->max_rows, B.v1 - B.v0);
+            P->max_slots = std::max(P->max_slots, B.e1 - B.e0);
+            v = w;
+        }
+    };
+    if (block_slots_hint > 0) {
+        plan(0.0, block_slots_hint);
+    } else {
+        double cap = 0.9 * (double)avail;
+        for (int attempt = 0; attempt < 16; ++attempt) {
+            plan(cap, 0);
+            if (60.0 * (double)P->max_rows + 36.0 * (double)P->max_slots <= 0.95 * (double)avail) break;
+            cap *= 0.85;
+        }
     }
     for (int k = 0; k < 3 && s == SCAN_OK; ++k) {
         s = dev_alloc(ctx, P->boff[k], 8 * ((size_t)P->max_rows + 1));
@@ -614,6 +643,7 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
             if (j != i) SCAN_TRY(release_slot(g, sj));
         }
     }
+    const int uf_limit = c->loop_limit ? (int)std::min<uint32_t>(c->loop_limit, kUfLimitP) : kUfLimitP;
     k_p_core<<<grid_for(n, 256), 256, 0, st>>>(ecnt, n, prm.mu, core, parent);
     c->launches++;
     // ---- pass 2: union-find, one block at a time
@@ -626,12 +656,12 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
         if (rows > 0) {
             k_p_hook<<<grid_for((int64_t)rows * 32, 256), 256, 0, st>>>(
                 (const int64_t *)P->boff[slot].ptr, (const int32_t *)P->badj[slot].ptr, B.v0, rows, B.e0, bits, core,
-                parent, err);
+                parent, err, uf_limit);
             c->launches++;
         }
         SCAN_TRY(release_slot(g, slot));
     }
-    k_p_final<<<grid_for(n, 256), 256, 0, st>>>(core, n, parent, cid, err);
+    k_p_final<<<grid_for(n, 256), 256, 0, st>>>(core, n, parent, cid, err, uf_limit);
     c->launches++;
     // ---- pass 3a: border memberships, block by block, pairs to the host.
     // A non-core vertex has at most mu - 2 similar neighbours besides itself.
