@@ -152,7 +152,7 @@ def test_every_strategy_gives_the_oracle_result(ps, ctx, which):
     dg = ctx.load(g)
     try:
         for strategy in (ps.SCAN_STRATEGY_FORWARD, ps.SCAN_STRATEGY_OWNER, ps.SCAN_STRATEGY_BSEARCH,
-                         ps.SCAN_STRATEGY_FORWARD_LEAN):
+                         ps.SCAN_STRATEGY_FORWARD_LEAN, ps.SCAN_STRATEGY_PROGRESSIVE):
             dg.set_strategy(strategy)
             for (p, q, mu) in [(1, 5, 2), (1, 2, 3), (7, 10, 5)]:
                 assert_same(dg.query(p, q, mu, ps.SCAN_Q_RECOMPUTE), oracle.scan_from_counts(g, cn, p, q, mu),
