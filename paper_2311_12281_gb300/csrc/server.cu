@@ -182,8 +182,8 @@ struct scan_server {
         }
         Graph *g = sg.g;
         sl.stream = g->nnz <= kSmallGraphSlots ? sl.hi : sl.lo;
-        uint32_t mode = SCAN_Q_RECOMPUTE;
-        if (opts.use_cache) {
+        uint32_t mode = opts.use_cache == 2 ? SCAN_Q_PLAIN : SCAN_Q_RECOMPUTE;
+        if (opts.use_cache == 1) {
             if (g->cache_valid) {
                 mode = SCAN_Q_AUTO;
             } else {
