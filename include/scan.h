@@ -162,6 +162,32 @@ SCAN_API int32_t scan_graph_blocks(const scan_graph *g);
  * total since it was loaded (validation and every query; Section 5's
  * transfer volume); 0 for a resident graph. */
 SCAN_API uint64_t scan_graph_transfer_bytes(const scan_graph *g);
+/*
+ * Zero-copy reading of a partitioned graph (enable != 0; 0 returns to
+ * copied blocks): the kernels read the streamed partner blocks of the
+ * similarity pass, and the blocks of the later passes, in place from the
+ * caller's pinned host CSR through the host link (NVLink-C2C on GB300),
+ * instead of copying each block into device memory first; the held block of
+ * each pass-1 row of pairs is still copied. The paper's Section 6.3 sets
+ * its partitioned design against a unified-memory version; this is that
+ * comparison's counterpart here. Results are identical either way (Lemma
+ * 5.1). SCAN_EINVAL for a resident graph; SCAN_ECUDA when the host arrays
+ * are not mapped for device access. Synchronises the context's stream.
+ */
+SCAN_API scan_status scan_graph_set_zero_copy(scan_graph *g, int32_t enable);
+/*
+ * The paper's own out-of-core partition (Section 5, Algorithm 5's CPU part,
+ * Definition "Edge Extended Subgraph"), planned on the host for comparison
+ * with the row-block pairs above: undirected edges (u, v), u < v, are taken
+ * in CSR order into the current subgraph with every edge incident to them;
+ * when Memof(G_s) + Memof(G'_s) + 15 |V(G)| would exceed device_bytes the
+ * subgraph is closed. Memof(G) = 25 |E(G)| + 4 |V(G)|. Returns the number of
+ * subgraphs and the bytes loading each of them once moves (the sum of their
+ * Memof). offsets int64[n+1] and adj int32[nnz] are host arrays, read only;
+ * no device work. SCAN_EINVAL on malformed offsets or ids out of range.
+ */
+SCAN_API scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                                             uint64_t device_bytes, int64_t *subgraphs, uint64_t *bytes);
 SCAN_API int32_t scan_graph_n(const scan_graph *g);
 SCAN_API int64_t scan_graph_nnz(const scan_graph *g);
 /* Device bytes held by this graph (including its count cache). */

@@ -81,6 +81,9 @@ SIGNATURES = {
     "scan_graph_load_partitioned": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64, _I64, _PP]),
     "scan_graph_blocks": (_I32, [_VP]),
     "scan_graph_transfer_bytes": (_U64, [_VP]),
+    "scan_graph_set_zero_copy": (ctypes.c_int, [_VP, _I32]),
+    "scan_plan_edge_extended": (ctypes.c_int, [_I32, _VP, _VP, _I64, _U64, ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_uint64)]),
     "scan_graph_n": (_I32, [_VP]),
     "scan_graph_nnz": (_I64, [_VP]),
     "scan_graph_device_bytes": (_U64, [_VP]),
@@ -230,6 +233,21 @@ def scan_graph_blocks(g: int) -> int:
 
 def scan_graph_transfer_bytes(g: int) -> int:
     return int(lib().scan_graph_transfer_bytes(g))
+
+
+def scan_graph_set_zero_copy(g: int, enable: bool):
+    _check(lib().scan_graph_set_zero_copy(g, 1 if enable else 0))
+
+
+def scan_plan_edge_extended(n: int, offsets: np.ndarray, adj: np.ndarray, device_bytes: int) -> tuple[int, int]:
+    """(subgraphs, bytes) of the paper's edge extended subgraph partition (host only)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    a = np.ascontiguousarray(adj, dtype=np.int32)
+    k = ctypes.c_int64()
+    b = ctypes.c_uint64()
+    _check(lib().scan_plan_edge_extended(int(n), off.ctypes.data, a.ctypes.data if a.size else None, int(a.size),
+                                         int(device_bytes), ctypes.byref(k), ctypes.byref(b)))
+    return k.value, b.value
 
 
 def scan_graph_n(g: int) -> int:
@@ -546,6 +564,9 @@ class Graph:
     @property
     def transfer_bytes(self) -> int:
         return scan_graph_transfer_bytes(self.handle)
+
+    def set_zero_copy(self, enable: bool):
+        scan_graph_set_zero_copy(self.handle, enable)
 
     def free(self):
         if self.handle:

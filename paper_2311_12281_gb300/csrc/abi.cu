@@ -425,6 +425,39 @@ int32_t scan_graph_blocks(const scan_graph *g) {
 
 uint64_t scan_graph_transfer_bytes(const scan_graph *g) { return g && g->part ? part_transfer_bytes(g) : 0; }
 
+scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                                    uint64_t device_bytes, int64_t *subgraphs, uint64_t *bytes) {
+    ABI_GUARD_BEGIN
+    if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj) || !subgraphs || !bytes) {
+        set_error("bad sizes or NULL arrays");
+        return SCAN_EINVAL;
+    }
+    if (n > 0 && (offsets[0] != 0 || offsets[n] != nnz)) {
+        set_error("offsets[0] must be 0 and offsets[n] must equal nnz");
+        return SCAN_EINVAL;
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (offsets[v + 1] < offsets[v]) {
+            set_error("invalid CSR offsets at index " + std::to_string(v + 1));
+            return SCAN_EINVAL;
+        }
+    for (int64_t s = 0; s < nnz; ++s)
+        if (adj[s] < 0 || adj[s] >= n) {
+            set_error("id out of range at slot " + std::to_string(s));
+            return SCAN_EINVAL;
+        }
+    return plan_edge_extended(n, offsets, adj, nnz, device_bytes, subgraphs, bytes);
+    ABI_GUARD_END
+}
+
+scan_status scan_graph_set_zero_copy(scan_graph *g, int32_t enable) {
+    ABI_GUARD_BEGIN
+    if (!g) { set_error("graph is NULL"); return SCAN_EINVAL; }
+    if (!g->part) { set_error("only a partitioned graph streams its CSR"); return SCAN_EINVAL; }
+    return part_set_zero_copy(g, enable != 0);
+    ABI_GUARD_END
+}
+
 void scan_graph_free(scan_graph *g) { graph_destroy(g); }
 
 int32_t scan_graph_n(const scan_graph *g) { return g ? g->n : 0; }

@@ -41,6 +41,12 @@ struct Part {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copied[3] = {nullptr, nullptr, nullptr};
     uint64_t h2d_bytes = 0;  // block copies issued since the load
+    // zero-copy mode: block slots 1 and 2 (the streamed partner and single
+    // blocks) are read by the kernels straight from the pinned host CSR
+    // through these device-side addresses, with no copy
+    bool zero_copy = false;
+    const int64_t *d_hoff = nullptr;
+    const int32_t *d_hadj = nullptr;
 };
 
 namespace {
@@ -372,6 +378,11 @@ static scan_status load_block(Graph *g, int slot, int bi, bool async) {
     Part *P = g->part;
     Ctx *c = g->ctx;
     if (P->loaded[slot] == bi) return SCAN_OK;
+    if (P->zero_copy && slot != 0) {  // read in place through the host link
+        P->loaded[slot] = bi;
+        P->pending[slot] = false;
+        return SCAN_OK;
+    }
     const Block &B = P->blocks[(size_t)bi];
     const int32_t rows = B.v1 - B.v0;
     cudaStream_t st = async ? P->copy_stream : c->stream;
@@ -398,6 +409,19 @@ static scan_status use_block(Graph *g, int slot, int bi) {
     return SCAN_OK;
 }
 
+// The offsets and ids of the block in a slot, as the kernels address them
+// (offsets global, ids from the block's first slot): the slot's device copy,
+// or in zero-copy mode the host CSR itself.
+static const int64_t *slot_off(const Part *P, int slot) {
+    if (P->zero_copy && slot != 0) return P->d_hoff + P->blocks[(size_t)P->loaded[slot]].v0;
+    return (const int64_t *)P->boff[slot].ptr;
+}
+
+static const int32_t *slot_adj(const Part *P, int slot) {
+    if (P->zero_copy && slot != 0) return P->d_hadj + P->blocks[(size_t)P->loaded[slot]].e0;
+    return (const int32_t *)P->badj[slot].ptr;
+}
+
 // Marks the end of the compute stream's use of a slot.
 static scan_status release_slot(Graph *g, int slot) {
     SCAN_CUDA(cudaEventRecord(g->part->copied[slot], g->ctx->stream));
@@ -407,6 +431,111 @@ static scan_status release_slot(Graph *g, int slot) {
 int32_t part_block_count(const Graph *g) { return g->part ? (int32_t)g->part->blocks.size() : 0; }
 
 uint64_t part_transfer_bytes(const Graph *g) { return g->part ? g->part->h2d_bytes : 0; }
+
+// ------------------------------------------------------------ the paper's partitioner
+// Section 5's edge extended subgraphs, planned on the host as Algorithm 5
+// does (its CPU part): the undirected edges (u, v), u < v, are taken in CSR
+// order into the current subgraph G_s together with every edge incident to
+// them (the rows of u and v); when Memof(G_s) + Memof(G'_s) + 15 |V(G)| would
+// exceed the device memory, G_s is closed and a new one started. Memof(G) =
+// 25 |E(G)| + 4 |V(G)| (the paper's CSR-enhanced layout). The subgraph's
+// edges are the union of the rows of the endpoints taken (`inrow`), its
+// vertices those rows' endpoints (`touched`); both are cleared through the
+// lists of what was marked, so a subgraph costs only what it holds.
+scan_status plan_edge_extended(int32_t n, const int64_t *off, const int32_t *adj, int64_t nnz, uint64_t mem,
+                               int64_t *subgraphs, uint64_t *bytes) {
+    std::vector<uint8_t> inrow((size_t)n, 0), touched((size_t)n, 0);
+    std::vector<int32_t> rows, verts;
+    const double fixed = 15.0 * (double)n;
+    double es = 0, vs = 0;  // edges and vertices of the current subgraph
+    int64_t k = 0;
+    double total = 0;
+    auto close = [&]() {
+        if (es == 0 && vs == 0) return;
+        total += 25.0 * es + 4.0 * vs;
+        ++k;
+        for (int32_t x : rows) inrow[(size_t)x] = 0;
+        for (int32_t x : verts) touched[(size_t)x] = 0;
+        rows.clear();
+        verts.clear();
+        es = vs = 0;
+    };
+    auto take = [&](int32_t x) {
+        if (inrow[(size_t)x]) return;
+        for (int64_t s = off[x]; s < off[x + 1]; ++s) {
+            const int32_t y = adj[s];
+            if (!inrow[(size_t)y]) es += 1;
+            if (!touched[(size_t)y]) {
+                touched[(size_t)y] = 1;
+                verts.push_back(y);
+                vs += 1;
+            }
+        }
+        if (!touched[(size_t)x]) {
+            touched[(size_t)x] = 1;
+            verts.push_back(x);
+            vs += 1;
+        }
+        inrow[(size_t)x] = 1;
+        rows.push_back(x);
+    };
+    for (int32_t u = 0; u < n; ++u) {
+        for (int64_t s = off[u]; s < off[u + 1]; ++s) {
+            const int32_t v = adj[s];
+            if (v <= u) continue;
+            if (inrow[(size_t)u] && inrow[(size_t)v]) continue;
+            // G'_s: take both rows, and if the subgraph no longer fits, undo
+            // them, close it, and take them into a new one
+            const size_t nr = rows.size(), nv = verts.size();
+            const double es0 = es, vs0 = vs;
+            take(u);
+            take(v);
+            const bool grew = es > es0 || vs > vs0;  // nothing new: the subgraph already holds G'_s
+            if (grew && 25.0 * es + 4.0 * vs + fixed > (double)mem && (es0 > 0 || vs0 > 0)) {
+                for (size_t i = nr; i < rows.size(); ++i) inrow[(size_t)rows[i]] = 0;
+                for (size_t i = nv; i < verts.size(); ++i) touched[(size_t)verts[i]] = 0;
+                rows.resize(nr);
+                verts.resize(nv);
+                es = es0;
+                vs = vs0;
+                close();
+                take(u);
+                take(v);
+            }
+        }
+    }
+    close();
+    (void)nnz;
+    *subgraphs = k;
+    *bytes = (uint64_t)total;
+    return SCAN_OK;
+}
+
+scan_status part_set_zero_copy(Graph *g, bool on) {
+    Part *P = g->part;
+    Ctx *c = g->ctx;
+    SCAN_CUDA(cudaSetDevice(c->device));
+    SCAN_CUDA(cudaStreamSynchronize(c->stream));
+    SCAN_CUDA(cudaStreamSynchronize(P->copy_stream));
+    if (on && g->n > 0 && !P->d_hoff) {
+        void *po = nullptr, *pa = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&po, (void *)P->h_off, 0);
+        if (e == cudaSuccess && g->nnz > 0) e = cudaHostGetDevicePointer(&pa, (void *)P->h_adj, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("the host CSR is not mapped for device access (pinned, mapped memory is needed)");
+            return SCAN_ECUDA;
+        }
+        P->d_hoff = (const int64_t *)po;
+        P->d_hadj = (const int32_t *)pa;
+    }
+    P->zero_copy = on && g->n > 0;
+    for (int k = 1; k < 3; ++k) {  // nothing is resident in the streamed slots any more
+        P->loaded[k] = -1;
+        P->pending[k] = false;
+    }
+    return SCAN_OK;
+}
 
 void part_release(Graph *g) {
     Part *P = g->part;
@@ -463,7 +592,10 @@ scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) return false;
         cudaGetLastError();
-        if (cudaHostRegister((void *)p, bytes, cudaHostRegisterReadOnly) == cudaSuccess) return true;
+        if (cudaHostRegister((void *)p, bytes, cudaHostRegisterReadOnly | cudaHostRegisterMapped) == cudaSuccess)
+            return true;
+        cudaGetLastError();
+        if (cudaHostRegister((void *)p, bytes, cudaHostRegisterMapped) == cudaSuccess) return true;
         cudaGetLastError();
         if (cudaHostRegister((void *)p, bytes, cudaHostRegisterDefault) == cudaSuccess) return true;
         cudaGetLastError();
@@ -636,7 +768,7 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
                 const int64_t bound = (int64_t)rows_i + (Bi.e1 - Bi.e0) + 1;
                 k_p_similar<<<grid_for(bound * 32, 256, sim_blocks), 256, 0, st>>>(
                     (const Chunk *)g->src.ptr, pos + rows_i, offi, adji, Bi.v0, Bi.e0,
-                    (const int64_t *)P->boff[sj].ptr, (const int32_t *)P->badj[sj].ptr, Bj.v0, Bj.e0, pp, qq, bits,
+                    slot_off(P, sj), slot_adj(P, sj), Bj.v0, Bj.e0, pp, qq, bits,
                     ecnt, err);
                 c->launches += 3;
             }
@@ -655,7 +787,7 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
         const int32_t rows = B.v1 - B.v0;
         if (rows > 0) {
             k_p_hook<<<grid_for((int64_t)rows * 32, 256), 256, 0, st>>>(
-                (const int64_t *)P->boff[slot].ptr, (const int32_t *)P->badj[slot].ptr, B.v0, rows, B.e0, bits, core,
+                slot_off(P, slot), slot_adj(P, slot), B.v0, rows, B.e0, bits, core,
                 parent, err, uf_limit);
             c->launches++;
         }
@@ -688,8 +820,8 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
             release_slot(g, slot);
             continue;
         }
-        auto *offb = (const int64_t *)P->boff[slot].ptr;
-        auto *adjb = (const int32_t *)P->badj[slot].ptr;
+        auto *offb = slot_off(P, slot);
+        auto *adjb = slot_adj(P, slot);
         int32_t *cnt = (int32_t *)g->cnt.ptr;
         int64_t *pos = (int64_t *)g->cnt_off.ptr;
         int32_t *ucnt = (int32_t *)g->ucnt.ptr;
@@ -729,7 +861,7 @@ scan_status part_query(Graph *g, const scan_params &prm, scan_result **out) {
         const int32_t rows = B.v1 - B.v0;
         if (rows > 0) {
             k_p_label<<<grid_for((int64_t)rows * 32, 256), 256, 0, st>>>(
-                (const int64_t *)P->boff[slot].ptr, (const int32_t *)P->badj[slot].ptr, B.v0, rows, B.e0, core,
+                slot_off(P, slot), slot_adj(P, slot), B.v0, rows, B.e0, core,
                 cid, mfirst, mmulti, label);
             c->launches++;
         }

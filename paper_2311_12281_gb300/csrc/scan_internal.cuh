@@ -237,6 +237,9 @@ scan_status part_query(Graph *g, const scan_params &p, scan_result **out);
 void part_release(Graph *g);
 int32_t part_block_count(const Graph *g);
 uint64_t part_transfer_bytes(const Graph *g);
+scan_status part_set_zero_copy(Graph *g, bool on);
+scan_status plan_edge_extended(int32_t n, const int64_t *off, const int32_t *adj, int64_t nnz, uint64_t mem,
+                               int64_t *subgraphs, uint64_t *bytes);
 
 #define SCAN_CUDA(call)                                              \
     do {                                                             \

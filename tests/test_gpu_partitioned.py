@@ -178,3 +178,39 @@ def test_partitioned_graph_cannot_join_a_batch(ps, ctx):
     finally:
         dp.free()
         dr.free()
+
+
+@pytest.mark.parametrize("name", ["rmat12", "chung_lu", "star_path", "union_with_isolated"])
+def test_zero_copy_reads_match_copied_blocks_and_oracle(ps, ctx, name):
+    # the streamed blocks read in place from the pinned host CSR (the host
+    # link instead of copies): same answers, fewer bytes copied
+    g = graphs()[name]
+    slots = max(64, g.nnz // 9)
+    dg = ctx.load_partitioned(g, block_slots=slots)
+    try:
+        assert dg.blocks > 1
+        for (p, q, mu) in PARAMS[:3]:
+            want = oracle.scan(g, p, q, mu)
+            b0 = dg.transfer_bytes
+            copied = dg.query(p, q, mu)
+            copied_bytes = dg.transfer_bytes - b0
+            dg.set_zero_copy(True)
+            b1 = dg.transfer_bytes
+            zc = dg.query(p, q, mu)
+            zc_bytes = dg.transfer_bytes - b1
+            dg.set_zero_copy(False)
+            assert_same(copied, want, f"{name} copied eps={p}/{q} mu={mu}")
+            assert_same(zc, want, f"{name} zero-copy eps={p}/{q} mu={mu}")
+            assert zc_bytes < copied_bytes
+    finally:
+        dg.free()
+
+
+def test_zero_copy_is_refused_for_a_resident_graph(ps, ctx):
+    dg = ctx.load(gg.rmat(8, 8, seed=1))
+    try:
+        with pytest.raises(ps.ScanError) as ei:
+            dg.set_zero_copy(True)
+        assert ei.value.status == ps.SCAN_EINVAL
+    finally:
+        dg.free()
