@@ -73,11 +73,14 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain GPU path comparator")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the R-MAT scale-14 and 4,096-graph batch summaries of the default run")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel choice (no autotuner)")
     ap.add_argument("--strategy", choices=["forward", "owner", "bsearch", "progressive", "lean"], default=None,
                     help="force a similarity kernel family (no autotuner) and report each query's time")
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["sweep", "batch", "serving", "outofcore", "small"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batch", "serving", "outofcore", "small", "plan"],
+                    default="sweep",
                     help="sweep: the R-MAT scale-22 sweep (default, the headline line); batch: 4,096 "
                          "Chung-Lu graphs in one pass; serving: Poisson query streams against the server")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -92,6 +95,8 @@ def parse():
     ap.add_argument("--ooc-scale", type=int, default=27, help="out of core: R-MAT scale")
     ap.add_argument("--ooc-budget-gb", type=float, default=8.0, help="out of core: device budget (GB)")
     ap.add_argument("--no-resident", action="store_true", help="out of core: skip the resident comparison")
+    ap.add_argument("--plan-scale", type=int, default=22, help="plan: R-MAT scale of the partition comparison")
+    ap.add_argument("--plan-budget-gb", type=float, default=1.0, help="plan: device budget (GB)")
     return ap.parse_args()
 
 
@@ -279,7 +284,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- batch
-def run_batch(args):
+def run_batch(args, emit: bool = True):
     """4,096 Chung-Lu graphs (exponent 2.1, n log-uniform in [100, 50000], mean
     degree uniform in [4, 64]), each with its own eps = p/20 and mu, clustered
     together in one pass over the resident union (kernel family and schedule
@@ -374,7 +379,9 @@ def run_batch(args):
             "gpu_launches": launches, "clocks": clk,
             "e2e": {"value": total_m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "s_per_step": e2e_s, "phases": phases}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------- serving
@@ -509,7 +516,7 @@ def run_serving(args):
 
 
 # --------------------------------------------------------------- small
-def run_small(args):
+def run_small(args, emit: bool = True):
     """R-MAT scale 14, edge factor 8, seed 1 (the oracle's seconds-scale case):
     median over 20 warm queries at eps = 1/2, mu = 3, each a full recompute."""
     import torch
@@ -563,7 +570,9 @@ def run_small(args):
             "plain_gpu": {"value": g.m / (out["plain"] / 1e3), "unit": UNIT, "ms_per_step": out["plain"]},
             "e2e": {"value": g.m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_query": e2e_ms,
                     "what": "host-result query through the ABI on the resident graph"}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------- out of core
@@ -614,6 +623,16 @@ def run_outofcore(args):
     r = dg.query(p, q, mu)
     query_s = time.perf_counter() - t
     query_h2d = dg.transfer_bytes - load_h2d
+    # the same query reading the streamed blocks in place over the host link
+    dg.set_zero_copy(True)
+    t = time.perf_counter()
+    h0 = dg.transfer_bytes
+    rz = dg.query(p, q, mu)
+    zc_s = time.perf_counter() - t
+    zc_h2d = dg.transfer_bytes - h0
+    dg.set_zero_copy(False)
+    zc_same = all(np.array_equal(r[k], rz[k]) for k in ("core", "cid", "label", "pairs"))
+    del rz
     link = host_to_device_peak(1 << 30)
     clk = clocks.stop()
     dev_peak = ctx.device_bytes
@@ -632,6 +651,9 @@ def run_outofcore(args):
                      "query_h2d_gbs": query_h2d / query_s / 1e9, "h2d_peak_gbs": link,
                      "frac": (query_h2d / query_s / 1e9) / link if link else None,
                      "peak_source": "pinned 1 GiB cudaMemcpy host-to-device, best of 5, CUDA events (this run)"},
+            "zero_copy": {"value": g.m / zc_s, "unit": UNIT, "query_s": zc_s, "copied_h2d_bytes": zc_h2d,
+                          "identical_to_copied": bool(zc_same),
+                          "what": "streamed blocks read in place from the pinned host CSR over the host link"},
             "device_bytes_after_query": dev_peak, "clocks": clk}
     if not args.no_resident:
         # the same query on the resident graph, element by element
@@ -650,6 +672,44 @@ def run_outofcore(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- partition comparison
+def run_plan(args):
+    """Transfer volume of one out-of-core query under a device budget: the
+    row-block pairs this library streams (measured: the host-to-device bytes
+    of one query), against the paper's edge extended subgraphs (Algorithm 5,
+    planned on the host: each subgraph loaded once, Memof = 25|E| + 4|V|)."""
+    import paper_2311_12281_gb300 as ps
+    from paper_2311_12281_gb300 import _build
+
+    _build.build()
+    g = gg.rmat(args.plan_scale, 16, seed=2)
+    budget = int(args.plan_budget_gb * (1 << 30))
+    with ps.Context(0, budget_bytes=budget) as ctx:
+        dg = ctx.load_partitioned(g)
+        h0 = dg.transfer_bytes
+        t = time.perf_counter()
+        dg.query(1, 2, 5)
+        q_s = time.perf_counter() - t
+        row_bytes = dg.transfer_bytes - h0
+        blocks = dg.blocks
+        dg.free()
+    t = time.perf_counter()
+    k, plan_bytes = ps.scan_plan_edge_extended(g.n, g.offsets, g.adj, budget)
+    plan_s = time.perf_counter() - t
+    csr = g.offsets.nbytes + g.adj.nbytes
+    line = {"metric": "out-of-core transfer bytes per query", "unit": "bytes", "higher_is_better": False,
+            "value": row_bytes, "n_gpus": 1, "data": "synthetic", "dtype": "i32", "vs_baseline": None,
+            "config": {"workload": f"rmat_s{args.plan_scale}_ef16_partition_plans", "n": g.n, "m": g.m,
+                       "device_budget_bytes": budget, "host_csr_bytes": csr, "eps": "1/2", "mu": 5},
+            "row_block_pairs": {"blocks": blocks, "bytes_per_query": row_bytes, "x_csr": row_bytes / csr,
+                                "query_s": q_s},
+            "edge_extended_subgraphs": {"subgraphs": k, "bytes_per_query": plan_bytes, "x_csr": plan_bytes / csr,
+                                        "planning_s_host": plan_s,
+                                        "what": "the paper's Algorithm 5 partition (host plan): each subgraph "
+                                                "loaded once, Memof = 25|E_s| + 4|V_s|"}}
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -663,6 +723,8 @@ def main():
         return run_outofcore(args)
     if args.workload == "small":
         return run_small(args)
+    if args.workload == "plan":
+        return run_plan(args)
 
     import torch
 
@@ -888,6 +950,15 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = oracle_baseline(g)
+    if rank == 0 and world == 1 and not args.no_extras and args.mode == "recompute" and not args.strategy:
+        # the other single-GPU workloads in the same run, summarised (their
+        # own lines: --workload small / batch)
+        small = run_small(args, emit=False)
+        batch = run_batch(argparse.Namespace(**{**vars(args), "steps": 3, "warmup": 3}), emit=False)
+        result["other_workloads"] = {
+            small["config"]["workload"]: {k: small[k] for k in ("value", "unit", "ms_per_step", "plain_gpu", "e2e")},
+            batch["config"]["workload"]: {k: batch[k] for k in ("value", "unit", "ms_per_step", "per_graph_loop",
+                                                                 "gpu_launches", "e2e")}}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:

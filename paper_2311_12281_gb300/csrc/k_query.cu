@@ -321,6 +321,8 @@ __global__ void __launch_bounds__(kBlock) k_prog_degree(const int32_t *__restric
 // The warps of these kernels screen 32 edges at a time, lane l on edge
 // (32 t + l) W + w for warp w of W (so the heavy edges of one row spread over
 // all warps), then intersect the edges that need it one after another.
+constexpr int32_t kProgCheap = 64;  // smaller degree of the edges intersected in the first pass
+
 #define PROG_EDGES_BEGIN                                                                              \
     const int lane = threadIdx.x & 31;                                                                \
     const int64_t W = (int64_t)gridDim.x * (kBlock / kWarp);                                          \
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) k_prog_core(const int64_t *__restrict_
                                                      const int32_t *__restrict__ src, const int32_t *__restrict__ deg,
                                                      const uint32_t *__restrict__ oe, int64_t m, QParams qp,
                                                      uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
-                                                     int32_t *lb, int32_t *ub) {
+                                                     int32_t *lb, int32_t *ub, int32_t dlo, int32_t dhi) {
     PROG_EDGES_BEGIN
         int32_t u = 0, v = 0;
         bool need = false;
@@ -342,8 +344,9 @@ __global__ void __launch_bounds__(kBlock) k_prog_core(const int64_t *__restrict_
             const uint32_t e = oe[i];
             u = src[e];
             v = adj[e];
+            const int32_t dm = min(deg[u], deg[v]);
             const uint32_t mu = qp.mu_of(u);
-            need = !(role_fixed(lb, ub, u, mu) && role_fixed(lb, ub, v, mu));
+            need = dm >= dlo && dm <= dhi && !(role_fixed(lb, ub, u, mu) && role_fixed(lb, ub, v, mu));
         }
         for (unsigned todo = __ballot_sync(0xffffffffu, need); todo; todo &= todo - 1) {
             const int j = __ffs(todo) - 1;
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kBlock) k_prog_union(const int64_t *__restrict
                                                       const uint32_t *__restrict__ oe, int64_t m, QParams qp,
                                                       uint8_t *__restrict__ state, uint8_t *__restrict__ simo,
                                                       const uint8_t *__restrict__ core, int32_t *parent, uint32_t *err,
-                                                      int limit) {
+                                                      int limit, int32_t dlo, int32_t dhi) {
     PROG_EDGES_BEGIN
         int32_t u = 0, v = 0;
         bool need = false;
@@ -383,7 +386,8 @@ __global__ void __launch_bounds__(kBlock) k_prog_union(const int64_t *__restrict
             const uint32_t e = oe[i];
             u = src[e];
             v = adj[e];
-            need = core[u] && core[v];
+            const int32_t dm = min(deg[u], deg[v]);
+            need = core[u] && core[v] && dm >= dlo && dm <= dhi;
         }
         for (unsigned todo = __ballot_sync(0xffffffffu, need); todo; todo &= todo - 1) {
             const int j = __ffs(todo) - 1;
@@ -888,10 +892,14 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
                 k_prog_degree<<<gm, kBlock, 0, st>>>(adj, src, (const int32_t *)g->deg.ptr, oe, m, qp,
                                                      (uint8_t *)g->sim.ptr, simo, nsim, (int32_t *)g->hst.ptr);
                 c->launches++;
-                k_prog_core<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
-                    off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, nsim,
-                    (int32_t *)g->hst.ptr);
-                c->launches++;
+                // the cheap edges first (smaller degree <= kProgCheap), so their outcomes fix
+                // roles before the expensive ones are looked at
+                for (int pass = 0; pass < 2; ++pass) {
+                    k_prog_core<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
+                        off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, nsim,
+                        (int32_t *)g->hst.ptr, pass ? kProgCheap + 1 : 0, pass ? INT32_MAX : kProgCheap);
+                    c->launches++;
+                }
             }
         } else if (!(mode & SCAN_Q_PLAIN) && g->strategy != SCAN_STRATEGY_OWNER &&
                    g->strategy != SCAN_STRATEGY_BSEARCH) {
@@ -933,11 +941,13 @@ scan_status query_pipeline(Graph *g, const QParams &qp, uint32_t mode, uint8_t *
         StageTimer t(c, SCAN_STAGE_CLUSTER);
         const int uf_limit = c->loop_limit ? (int)std::min<uint32_t>(c->loop_limit, kUfLimit) : kUfLimit;
         if (m > 0) k_uf_hook<<<gs, kBlock, 0, st>>>(adj, src, oe, m, simo, core, parent, err, uf_limit);
-        if (m > 0 && progressive) {
-            k_prog_union<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
-                off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, core, parent, err,
-                uf_limit);
-            c->launches++;
+        if (m > 0 && progressive) {  // cheap edges first: they join trees the expensive ones then skip
+            for (int pass = 0; pass < 2; ++pass) {
+                k_prog_union<<<grid_for(m, kBlock, c->num_sms * 16), kBlock, 0, st>>>(
+                    off, adj, src, (const int32_t *)g->deg.ptr, oe, m, qp, (uint8_t *)g->sim.ptr, simo, core, parent,
+                    err, uf_limit, pass ? kProgCheap + 1 : 0, pass ? INT32_MAX : kProgCheap);
+                c->launches++;
+            }
         }
         k_uf_final<<<gt, kBlock, 0, st>>>(core, n, parent, cid, err, uf_limit);
         c->launches += 1 + (m > 0);
