@@ -155,23 +155,8 @@ __global__ void __launch_bounds__(256) k_p_similar(const Chunk *__restrict__ chu
             const bool never = dev::prune_dissimilar(a1 < b1 ? a1 : b1, a1 < b1 ? b1 : a1, pp, qq);
             const bool always = !never && dev::prune_similar(a1, b1, pp, qq);
             int c = 0;
-            if (!never && !always) {
-                // smaller row probes the larger by binary search
-                const int32_t *sm = du <= dv ? ru : rv, *lg = du <= dv ? rv : ru;
-                const int32_t ds = du <= dv ? du : dv, dl = du <= dv ? dv : du;
-                for (int32_t x = lane; x < ds; x += 32) {
-                    const int32_t key = sm[x];
-                    int32_t lo = 0, hi = dl;
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        const int32_t y = lg[mid];
-                        if (y < key) lo = mid + 1;
-                        else if (y > key) hi = mid;
-                        else { ++c; break; }
-                    }
-                }
-                c = __reduce_add_sync(0xffffffffu, c) + 2;
-            }
+            if (!never && !always)  // rows of similar length merged, else the shorter probed in the longer
+                c = dev::warp_common(ru, du, rv, dv) + 2;
             // mirror slot: position of u in row v, looked up for every edge (its
             // absence means an asymmetric input). The warp narrows the range 32
             // pivots at a time, then checks the last 32 positions at once.

@@ -328,5 +328,60 @@ __device__ __forceinline__ bool rank_less(int32_t du, int32_t u, int32_t dv, int
     return du < dv || (du == dv && u < v);
 }
 
+// |a cap b| of two ascending rows of distinct ids, computed by a whole warp
+// (every lane gets the count). Rows of similar length are merged 32 ids at a
+// time: each step loads a window of each row (coalesced), every id of the
+// window with the smaller maximum is looked up in the other window by a
+// 5-step search over the lanes' registers, and both windows advance past
+// that maximum, so each step settles at least one window. A row more than
+// 16 times shorter than the other is probed instead, each lane binary
+// searching its ids in the longer row. Bounded by na + nb steps.
+__device__ __forceinline__ int32_t warp_common(const int32_t *__restrict__ a, int32_t na,
+                                               const int32_t *__restrict__ b, int32_t nb) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (na > nb) {
+        const int32_t *t = a;
+        a = b;
+        b = t;
+        const int32_t tn = na;
+        na = nb;
+        nb = tn;
+    }
+    int c = 0;
+    if ((int64_t)nb > 16 * (int64_t)na) {
+        for (int32_t k = lane; k < na; k += 32) {
+            const int32_t x = __ldg(a + k);
+            int32_t lo = 0, hi = nb;
+            for (int it = 0; it < 40 && lo < hi; ++it) {
+                const int32_t mid = (lo + hi) >> 1;
+                const int32_t y = __ldg(b + mid);
+                if (y < x) lo = mid + 1;
+                else if (y > x) hi = mid;
+                else {
+                    ++c;
+                    break;
+                }
+            }
+        }
+        return __reduce_add_sync(full, c);
+    }
+    int32_t ia = 0, ib = 0;
+    for (int64_t guard = 0; guard <= (int64_t)na + nb && ia < na && ib < nb; ++guard) {
+        const int32_t x = ia + lane < na ? __ldg(a + ia + lane) : INT32_MAX;
+        const int32_t y = ib + lane < nb ? __ldg(b + ib + lane) : INT32_MAX;
+        const int32_t lim = min(__shfl_sync(full, x, 31), __shfl_sync(full, y, 31));
+        int pos = 0;  // ids of the y window below x (the window is ascending)
+#pragma unroll
+        for (int s = 16; s; s >>= 1)
+            if (__shfl_sync(full, y, pos + s - 1) < x) pos += s;
+        const int32_t yp = __shfl_sync(full, y, pos);
+        c += (x <= lim && x != INT32_MAX && yp == x) ? 1 : 0;
+        ia += __popc(__ballot_sync(full, x <= lim && ia + lane < na));
+        ib += __popc(__ballot_sync(full, y <= lim && ib + lane < nb));
+    }
+    return __reduce_add_sync(full, c);
+}
+
 }  // namespace dev
 }  // namespace scan
