@@ -35,10 +35,12 @@ __device__ __forceinline__ int contains(const int32_t *__restrict__ r, int32_t l
     return 0;
 }
 
-// Warp per degree-oriented edge (u, v), deg(u) <= deg(v): each lane takes
-// elements of nbr(u) and binary-searches them in nbr(v) (checkSim of
-// Algorithm 2, with the exact test). PRUNE skips edges whose outcome the
-// degrees fix; WRITE_SIM / WRITE_CN select the outputs.
+// Warp per degree-oriented edge (u, v), deg(u) <= deg(v). Without PRUNE
+// (the plain comparator) each lane takes elements of nbr(u) and
+// binary-searches them in nbr(v), as checkSim of Algorithm 2 does (with the
+// exact test). With PRUNE (the BSEARCH family) edges whose outcome the
+// degrees fix are skipped, and rows of similar length are merged by the warp
+// (dev::warp_common). WRITE_SIM / WRITE_CN select the outputs.
 template <bool PRUNE, bool WRITE_SIM, bool WRITE_CN>
 __global__ void __launch_bounds__(kBlock) k_isect_bsearch(
     const int64_t *__restrict__ off, const int32_t *__restrict__ adj, const int32_t *__restrict__ src,
@@ -62,8 +64,12 @@ __global__ void __launch_bounds__(kBlock) k_isect_bsearch(
         const int32_t *ru = adj + off[u];
         const int32_t *rv = adj + off[v];
         int c = 0;
-        for (int32_t k = lane; k < du; k += kWarp) c += contains(rv, dv, __ldg(ru + k));
-        c = __reduce_add_sync(0xffffffffu, c) + 2;
+        if (PRUNE) {  // the pruned family merges rows of similar length
+            c = dev::warp_common(ru, du, rv, dv) + 2;
+        } else {      // the plain comparator: binary search of every id of nbr(u) in nbr(v)
+            for (int32_t k = lane; k < du; k += kWarp) c += contains(rv, dv, __ldg(ru + k));
+            c = __reduce_add_sync(0xffffffffu, c) + 2;
+        }
         if (lane == 0) {
             if (WRITE_CN) { cn[e] = c; cn[rev[e]] = c; }
             if (WRITE_SIM && dev::eps_similar((uint64_t)c, (uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) {
@@ -268,21 +274,14 @@ __global__ void k_uf_final(const uint8_t *__restrict__ core, int32_t n, int32_t 
 // lb as its eps-degree. After it, only core-core edges between different
 // union-find trees and core-non-core edges still need their similarity.
 
-// exact closed count of the edge (u, v), the smaller row probed in the larger
-// (the whole warp), and the eps-test
+// exact closed count of the edge (u, v) by the whole warp (rows merged, or
+// the shorter probed in the longer), and the eps-test
 __device__ __forceinline__ bool warp_eps_edge(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                               int32_t u, int32_t v, int32_t du, int32_t dv, uint64_t pp,
                                               uint64_t qq) {
-    const int lane = threadIdx.x & 31;
     if (dev::prune_dissimilar((uint64_t)min(du, dv) + 1, (uint64_t)max(du, dv) + 1, pp, qq)) return false;
     if (dev::prune_similar((uint64_t)du + 1, (uint64_t)dv + 1, pp, qq)) return true;
-    const int32_t a = du <= dv ? u : v, b = du <= dv ? v : u;
-    const int32_t da = min(du, dv), db = max(du, dv);
-    const int32_t *ra = adj + off[a];
-    const int32_t *rb = adj + off[b];
-    int c = 0;
-    for (int32_t k = lane; k < da; k += kWarp) c += contains(rb, db, __ldg(ra + k));
-    c = __reduce_add_sync(0xffffffffu, c) + 2;
+    const int c = dev::warp_common(adj + off[u], du, adj + off[v], dv) + 2;
     return dev::eps_similar((uint64_t)c, (uint64_t)du + 1, (uint64_t)dv + 1, pp, qq);
 }
 
@@ -319,8 +318,10 @@ __global__ void __launch_bounds__(kBlock) k_prog_degree(const int32_t *__restric
 }
 
 // The warps of these kernels screen 32 edges at a time, lane l on edge
-// (32 t + l) W + w for warp w of W (so the heavy edges of one row spread over
-// all warps), then intersect the edges that need it one after another.
+// (32 t + l) W + w for warp w of W, so the heavy edges of one row spread
+// over all warps (consecutive tiles measured 10-40 % slower: a hub's row
+// then lands on few warps), and intersect the edges that need it one after
+// another.
 constexpr int32_t kProgCheap = 64;  // smaller degree of the edges intersected in the first pass
 
 #define PROG_EDGES_BEGIN                                                                              \
