@@ -5,10 +5,16 @@ temporary copy of ``oracle/scan_oracle.c``, compiled next to the brute force,
 and run through a short battery of the pins (the reconstructed Figure-1
 fixture, the matrix-square counts, the eps boundary, the brute force on every
 graph of up to 5 vertices).
+
+A mutant may read outside its arrays (a row search that runs past the last
+row does), so each compiled copy runs its pins in a child process: exit 10 is
+"every pin passed", exit 11 "a pin failed", and death by a signal is a failure
+too. Any other exit (an exception in the harness exits 1) fails the test.
 """
 import ctypes
 import os
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -44,7 +50,11 @@ def _compile(tmp_path, name, src_text):
     so = tmp_path / f"lib{name}.so"
     subprocess.run(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-o", str(so), str(src),
                     os.path.join(ROOT, "oracle", "brute.c")], check=True)
-    lib = ctypes.CDLL(str(so))
+    return str(so)
+
+
+def _load(so):
+    lib = ctypes.CDLL(so)
     vp, i64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int
     lib.oracle_common_counts.argtypes = [i64, vp, vp, vp, i32]
     lib.oracle_counts_for_slots.argtypes = [i64, vp, vp, vp, i64, vp, i32]
@@ -109,9 +119,20 @@ def _pins_pass(lib) -> bool:
     return True
 
 
+def _pins_pass_in_child(so) -> bool:
+    tests = os.path.dirname(os.path.abspath(__file__))
+    code = ("import sys; sys.path[:0] = [{!r}, {!r}]; import test_oracle_mutants as t; "
+            "sys.exit(10 if t._pins_pass(t._load({!r})) else 11)").format(ROOT, tests, so)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, OMP_NUM_THREADS="1"))
+    if r.returncode in (10, 11) or r.returncode < 0:
+        return r.returncode == 10
+    raise AssertionError(f"pin harness failed (exit {r.returncode}):\n{r.stderr[-2000:]}")
+
+
 def test_unmodified_copy_passes(tmp_path):
     text = open(os.path.join(ROOT, "oracle", "scan_oracle.c")).read()
-    assert _pins_pass(_compile(tmp_path, "orig", text))
+    assert _pins_pass_in_child(_compile(tmp_path, "orig", text))
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -119,5 +140,5 @@ def test_mutant_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
     text = open(os.path.join(ROOT, "oracle", "scan_oracle.c")).read()
     assert text.count(old) == 1, f"mutation site for '{name}' not found once"
-    lib = _compile(tmp_path, "mut", text.replace(old, new))
-    assert not _pins_pass(lib), f"planted mistake '{name}' passed every pin"
+    so = _compile(tmp_path, "mut", text.replace(old, new))
+    assert not _pins_pass_in_child(so), f"planted mistake '{name}' passed every pin"
