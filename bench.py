@@ -920,13 +920,19 @@ def main():
         adj_pin = torch.from_numpy(g.adj).pin_memory()
         h2d = off_pin.numel() * 8 + adj_pin.numel() * 4
 
+        e2e_phases = {}
+
         def e2e_step():
+            t0 = time.perf_counter()
             h = ps.scan_graph_load(ctx.handle, g.n, off_pin.numpy(), adj_pin.numpy())
+            t1 = time.perf_counter()
             d2h = 0
             for (p, q, mu) in queries:
                 r = ps.scan_query_ex(h, p, q, mu, mode if args.mode != "cache" else ps.SCAN_Q_BUILD_CACHE)
                 d2h += r["core"].nbytes + r["cid"].nbytes + r["label"].nbytes + r["pairs"].nbytes + 8
+            t2 = time.perf_counter()
             ps.scan_graph_free(h)
+            e2e_phases.update(load_s=t1 - t0, queries_s=t2 - t1, free_s=time.perf_counter() - t2)
             return d2h
 
         e2e_step()
@@ -943,7 +949,7 @@ def main():
         if dist:
             e2e_s = max_over_ranks(e2e_s, dist)
         result["e2e"] = {"value": replica_rate(edges_per_step, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                         "d2h_bytes_per_step": d2h, "s_per_step": e2e_s}
+                         "d2h_bytes_per_step": d2h, "s_per_step": e2e_s, "phases_last_step": e2e_phases}
 
     dg.free()
     ctx.close()

@@ -36,8 +36,8 @@ constexpr int kFwdUnroll = 8;
 constexpr unsigned long long kSlotEmpty = ~0ull;
 
 // CTA item classes by the owner's out-degree: 0 up to 256 (128-thread CTAs,
-// 8 KB tables), 1 up to 1024 (512 threads, 32 KB), 2 above (512 threads,
-// tables of 4096-key chunks, 128 KB)
+// 8 KB tables), 1 up to 1024 (256 threads, hash tables up to 32 KB), 2 above
+// (512 threads, tables of 4096-key chunks, 128 KB)
 __host__ __device__ __forceinline__ int fwd_class(int32_t ob) { return ob <= 256 ? 0 : (ob <= 1024 ? 1 : 2); }
 
 // log2 of the hash slots of a class's tables (8 bytes per slot: 8, 32 and
@@ -1665,11 +1665,14 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
         for (int cls = 2; cls >= 0; --cls) {
             const int64_t ni = g->fwd_items_n[cls];
             if (ni == 0) continue;
-            // 8 bytes per slot (key + count). Class 0: four slots per key, 8 KB,
-            // 128-thread CTAs (sixteen per SM: these owners hold little work,
-            // and small CTAs wait less at their barriers). Class 1: eight slots
-            // per key up to 512 keys, four above, 32 KB (four 512-thread CTAs
-            // per SM). Class 2: four per key, 128 KB.
+            // Hash tables take 8 bytes per slot (key + count). Class 0: four
+            // slots per key, 8 KB, 128-thread CTAs (sixteen per SM: these owners
+            // hold little work, and small CTAs wait less at their barriers).
+            // Class 1: eight slots per key up to 512 keys, four above, 32 KB;
+            // its items mostly take bitmaps of a few KB, on 256-thread CTAs
+            // (eight per SM: 1.3 % faster than four 512-thread ones). Class 2:
+            // four per key, 128 KB, 512-thread CTAs. The launch takes only the
+            // shared memory of the class's largest table.
             const int cap_logs = fwd_cap_logs(cls), load_shift = fwd_load_shift(cls);
             const size_t full = (size_t)(2 * sizeof(int)) << cap_logs;
             const size_t smem = g->fwd_smem_words[cls] > 0 ? std::min(full, 4 * (size_t)g->fwd_smem_words[cls]) : full;
@@ -1680,6 +1683,10 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
             if (cls == 0) {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 k_fwd_ent<128><<<(unsigned)ni, 128, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                                                                cap_logs, load_shift);
+            } else if (cls == 1) {
+                SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
                                                                 cap_logs, load_shift);
             } else {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
