@@ -260,6 +260,24 @@ SCAN_API scan_status scan_graph_autotune(scan_graph *g, const char *cache_path, 
 SCAN_API scan_status scan_query(scan_graph *g, uint32_t eps_num, uint32_t eps_den, uint32_t mu, scan_result **out);
 SCAN_API scan_status scan_query_ex(scan_graph *g, const scan_params *params, uint32_t mode, scan_result **out);
 
+/*
+ * Parameter sweep: k >= 1 queries (params[0..k-1], one mode for all) on one
+ * graph, answered in order; outs[j] receives what scan_query_ex(g,
+ * &params[j], mode, ...) would return (Definitions 2.1-2.6 at each (eps,
+ * mu); the parameter study of Section 6 runs such sweeps). Each result's copy
+ * to the host overlaps the next query's computation: the queries alternate
+ * between the graph's output buffers and a second set of 6(n+1) + 8 nnz
+ * bytes, allocated by the first sweep on the graph and kept (counted in
+ * scan_graph_device_bytes) until scan_graph_free. When that set does not fit
+ * the device or the budget, and for a partitioned graph, the queries run one
+ * at a time. Every params[j] is checked first (SCAN_EINVAL, nothing run);
+ * on any failure every result is freed and every outs[j] is NULL. The
+ * results are the caller's (scan_result_free each). Synchronous; not to be
+ * called concurrently with another query on the same graph.
+ */
+SCAN_API scan_status scan_query_sweep(scan_graph *g, const scan_params *params, int32_t k, uint32_t mode,
+                                      scan_result **outs);
+
 SCAN_API int32_t scan_result_n(const scan_result *r);
 SCAN_API const uint8_t *scan_result_core(const scan_result *r);     /* [n] 1 = core */
 SCAN_API const int32_t *scan_result_cluster(const scan_result *r);  /* [n] cluster id for cores, -1 otherwise */

@@ -96,6 +96,7 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_double)]),
     "scan_query": (ctypes.c_int, [_VP, _U32, _U32, _U32, _PP]),
     "scan_query_ex": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, _PP]),
+    "scan_query_sweep": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _U32, _VP]),
     "scan_query_device": (ctypes.c_int, [_VP, ctypes.POINTER(scan_params), _U32, ctypes.POINTER(scan_device_out)]),
     "scan_batch_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _U32, _PP]),
     "scan_batch_size": (_I32, [_VP]),
@@ -351,6 +352,15 @@ def scan_query_ex(g: int, eps_num: int, eps_den: int, mu: int, mode: int = SCAN_
     return _result_to_numpy(out.value)
 
 
+def scan_query_sweep(g: int, params, mode: int = SCAN_Q_AUTO) -> list:
+    """params: [(eps_num, eps_den, mu)]; one result dict per query, in order
+    (each result's copy to the host overlaps the next query)."""
+    k = len(params)
+    outs = (ctypes.c_void_p * max(k, 1))()
+    _check(lib().scan_query_sweep(g, _params_array(params) if k else None, k, mode, outs))
+    return [_result_to_numpy(outs[j]) for j in range(k)]
+
+
 def scan_query_device(g: int, eps_num: int, eps_den: int, mu: int, mode: int, core: int, cid: int, label: int,
                       pairs: int, pairs_cap: int, npairs: int):
     """Device-resident query into caller-owned device buffers (addresses)."""
@@ -543,6 +553,9 @@ class Graph:
 
     def query(self, eps_num: int, eps_den: int, mu: int, mode: int = SCAN_Q_AUTO) -> dict:
         return scan_query_ex(self.handle, eps_num, eps_den, mu, mode)
+
+    def sweep(self, params, mode: int = SCAN_Q_AUTO) -> list:
+        return scan_query_sweep(self.handle, params, mode)
 
     def drop_cache(self):
         scan_graph_drop_cache(self.handle)

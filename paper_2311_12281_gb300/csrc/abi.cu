@@ -55,6 +55,7 @@ void dev_free(Ctx *c, DevBuf &b) {
 static void graph_release(Graph *g) {
     Ctx *c = g->ctx;
     query_graph_drop(g);
+    sweep_release(g);
     g->for_each_buf([c](DevBuf &b) { dev_free(c, b); });
     if (g->h_npairs) cudaFreeHost(g->h_npairs);
     if (g->h_err) cudaFreeHost(g->h_err);

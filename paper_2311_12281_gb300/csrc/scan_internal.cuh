@@ -110,6 +110,13 @@ struct Graph {
     // host staging
     int64_t *h_npairs = nullptr; // pinned
     uint32_t *h_err = nullptr;   // pinned
+    // the second output set of a parameter sweep (scan_query_sweep), made on
+    // first use: one query writes it while the other set is copied to the host
+    DevBuf core2, cid2, label2, pairs2, npairs2;
+    cudaStream_t sweep_stream = nullptr;    // the copies to the host
+    cudaEvent_t sweep_done[2] = {nullptr, nullptr};    // a set's query finished
+    cudaEvent_t sweep_copied[2] = {nullptr, nullptr};  // a set's copies finished
+    int64_t *h_sweep_np = nullptr;          // pinned int64[2]: pair counts of the two sets
 
     template <class F>
     void for_each_buf(F f) {
@@ -117,7 +124,8 @@ struct Graph {
                           &items[2], &items[3], &owners_chunked, &acc, &foff, &fadj, &fin, &fcnt, &fsrc, &fhid, &fwd_qctr, &fwd_owners,
                           &fwd_items[0], &fwd_items[1], &fwd_items[2], &fwd_ebase, &fwd_elen, &fwd_efin, &heavy,
                           &qparams, &sim, &simo, &nsim, &hst, &mslots, &core, &cid, &parent, &label,
-                          &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err};
+                          &cnt, &cnt_off, &ucnt, &pair_off, &raw, &pairs, &npairs, &scan_tmp, &err,
+                          &core2, &cid2, &label2, &pairs2, &npairs2};
         for (DevBuf *b : bufs) f(*b);
     }
 };
@@ -234,6 +242,7 @@ bool result_set_pairs(scan_result *r, int64_t k);  // room for k pairs (r->k = k
 scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz, Graph **out,
                         int64_t block_slots_hint);
 scan_status part_query(Graph *g, const scan_params &p, scan_result **out);
+void sweep_release(Graph *g);  // the sweep's stream, events and pinned counts (sweep.cu)
 void part_release(Graph *g);
 int32_t part_block_count(const Graph *g);
 uint64_t part_transfer_bytes(const Graph *g);
