@@ -56,6 +56,7 @@ static void graph_release(Graph *g) {
     Ctx *c = g->ctx;
     query_graph_drop(g);
     sweep_release(g);
+    fwd_release(g);
     g->for_each_buf([c](DevBuf &b) { dev_free(c, b); });
     if (g->h_npairs) cudaFreeHost(g->h_npairs);
     if (g->h_err) cudaFreeHost(g->h_err);

@@ -1601,6 +1601,42 @@ scan_status fwd_prepare(Graph *g) {
     return SCAN_OK;
 }
 
+void fwd_release(Graph *g) {
+    if (g->fwd_side) cudaStreamDestroy(g->fwd_side);
+    if (g->fwd_fork) cudaEventDestroy(g->fwd_fork);
+    if (g->fwd_join) cudaEventDestroy(g->fwd_join);
+    g->fwd_side = nullptr;
+    g->fwd_fork = nullptr;
+    g->fwd_join = nullptr;
+}
+
+// The side stream of the per-class launches, when the query's stream has the
+// default priority (a prioritised stream, as the server's, keeps every launch
+// on itself). Null: no fork.
+static cudaStream_t fwd_side_stream(Graph *g, cudaStream_t st) {
+    int prio = 0;
+    if (cudaStreamGetPriority(st, &prio) != cudaSuccess || prio != 0) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!g->fwd_side) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (s) cudaStreamDestroy(s);
+            if (a) cudaEventDestroy(a);
+            return nullptr;
+        }
+        g->fwd_side = s;
+        g->fwd_fork = a;
+        g->fwd_join = b;
+    }
+    return g->fwd_side;
+}
+
 scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QParams &qp, int32_t *cn,
                               uint64_t *dd) {
     Ctx *c = g->ctx;
@@ -1662,9 +1698,20 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
         c->launches++;
         small_done = true;
     } else if (use_entries) {
+        // Class 2 (a few large owners: at scale 22, six CTAs for 0.2 ms) and
+        // then the warp owners run on the side stream while classes 1 and 0
+        // run on the query's: the class-2 CTAs would otherwise hold a handful
+        // of SMs while the rest idle. The counts are atomic, so the launches
+        // may overlap; the finish waits for both streams.
+        cudaStream_t side = fwd_side_stream(g, st);
+        if (side) {
+            SCAN_CUDA(cudaEventRecord(g->fwd_fork, st));
+            SCAN_CUDA(cudaStreamWaitEvent(side, g->fwd_fork, 0));
+        }
         for (int cls = 2; cls >= 0; --cls) {
             const int64_t ni = g->fwd_items_n[cls];
             if (ni == 0) continue;
+            const cudaStream_t cs = (side && cls == 2) ? side : st;
             // Hash tables take 8 bytes per slot (key + count). Class 0: four
             // slots per key, 8 KB, 128-thread CTAs (sixteen per SM: these owners
             // hold little work, and small CTAs wait less at their barriers).
@@ -1682,18 +1729,28 @@ scan_status launch_fwd_counts(Graph *g, bool write_sim, bool write_cn, const QPa
             auto *ef = (const uint32_t *)g->fwd_efin.ptr;
             if (cls == 0) {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<128><<<(unsigned)ni, 128, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                k_fwd_ent<128><<<(unsigned)ni, 128, smem, cs>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
                                                                 cap_logs, load_shift);
             } else if (cls == 1) {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<256><<<(unsigned)ni, 256, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                k_fwd_ent<256><<<(unsigned)ni, 256, smem, cs>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
                                                                 cap_logs, load_shift);
             } else {
                 SCAN_CUDA(cudaFuncSetAttribute(k_fwd_ent<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_fwd_ent<512><<<(unsigned)ni, 512, smem, st>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
+                k_fwd_ent<512><<<(unsigned)ni, 512, smem, cs>>>(items, foff, fadj, fhid, eb, el, ef, fcnt,
                                                                 cap_logs, load_shift);
             }
             c->launches++;
+        }
+        if (side) {
+            if (g->fwd_small > 0) {
+                k_fwd_small<<<grid_for((int64_t)g->fwd_small * kWarp, 256, c->num_sms * 16), 256, 0, side>>>(
+                    (const int32_t *)g->fwd_owners.ptr, g->fwd_small, off, adj, deg, foff, fadj, fin, fcnt, rs);
+                c->launches++;
+            }
+            small_done = true;
+            SCAN_CUDA(cudaEventRecord(g->fwd_join, side));
+            SCAN_CUDA(cudaStreamWaitEvent(st, g->fwd_join, 0));
         }
     }
     auto kern = k_fwd_cta<512>;

@@ -79,6 +79,10 @@ struct Graph {
     int32_t fwd_smem_words[3] = {0, 0, 0};  // shared memory the largest table of each item class needs
     bool fwd_queue = false;  // count in one persistent launch over a work queue (else one launch per class)
     DevBuf fwd_qctr;        // its take counters
+    // the per-class launches: class 2 and the warp owners run on a side
+    // stream beside classes 1 and 0 (forked from and joined to the query's stream)
+    cudaStream_t fwd_side = nullptr;
+    cudaEvent_t fwd_fork = nullptr, fwd_join = nullptr;
     int64_t fwd_small_work = 1 << 15;  // owners with out-degree <= 64 and at most this many probes: one warp
     int64_t fwd_item_work = 1 << 20;   // target probes per CTA work item
     int strategy = 0;       // similarity kernel family: SCAN_STRATEGY_*
@@ -243,6 +247,7 @@ scan_status part_create(Ctx *ctx, int32_t n, const int64_t *offsets, const int32
                         int64_t block_slots_hint);
 scan_status part_query(Graph *g, const scan_params &p, scan_result **out);
 void sweep_release(Graph *g);  // the sweep's stream, events and pinned counts (sweep.cu)
+void fwd_release(Graph *g);    // the counting stage's side stream and events (k_fwd.cu)
 void part_release(Graph *g);
 int32_t part_block_count(const Graph *g);
 uint64_t part_transfer_bytes(const Graph *g);
