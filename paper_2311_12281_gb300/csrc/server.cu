@@ -157,6 +157,11 @@ struct scan_server {
             Graph *g = nullptr;
             scan_status s = graph_create(ctx, sg.n, sg.h_off, sg.h_adj, sg.nnz, false, &g);
             if (s == SCAN_OK) s = fwd_prepare(g);
+            // the slots' streams read what the load stream wrote: finish it here
+            if (s == SCAN_OK) {
+                const cudaError_t e = cudaStreamSynchronize(load_stream);
+                if (e != cudaSuccess) s = cuda_fail(e, "graph load");
+            }
             if (s == SCAN_OK) {
                 sg.g = g;
                 std::lock_guard<std::mutex> lock(mu);
