@@ -325,7 +325,8 @@ def run_batch(args, emit: bool = True):
         t0 = time.perf_counter()
         bh = ps.scan_batch_load(ctx.handle, graphs)
         t1 = time.perf_counter()
-        res = ps.scan_batch_query(bh, params)
+        # one packed host result: each graph's arrays are views into it
+        res = ps.scan_batch_query_packed(bh, params)
         t2 = time.perf_counter()
         ps.scan_batch_free(bh)
         phases.update(load_s=t1 - t0, query_s=t2 - t1, free_s=time.perf_counter() - t2)

@@ -330,6 +330,16 @@ SCAN_API scan_graph *scan_batch_union(scan_batch *b);
 /* params[k]: graph j's eps, mu. outs[k] receive one result per graph (each
  * freed with scan_result_free). On failure no result is returned. */
 SCAN_API scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t mode, scan_result **outs);
+/* The same answers as scan_batch_query, as ONE result over the k graphs in
+ * batch order, with no per-graph host objects. Graph j owns the vertex range
+ * [vertex_offsets[j], vertex_offsets[j+1]) of core, cluster and label (its
+ * cluster ids are its own: the smallest core id of the cluster within graph
+ * j, -1 for a non-core) and the pair range [pair_offsets[j],
+ * pair_offsets[j+1]) of the border pairs (its own vertex and cluster ids,
+ * sorted). vertex_offsets and pair_offsets are caller arrays of k + 1
+ * entries. The result is the caller's (scan_result_free). */
+SCAN_API scan_status scan_batch_query_packed(scan_batch *b, const scan_params *params, uint32_t mode,
+                                             scan_result **out, int64_t *vertex_offsets, int64_t *pair_offsets);
 /* Device-resident form: writes the union's result (union ids) into device
  * buffers sized for the union, on the context's stream, without syncing. */
 SCAN_API scan_status scan_batch_query_device(scan_batch *b, const scan_params *params, uint32_t mode,

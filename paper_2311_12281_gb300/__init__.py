@@ -102,6 +102,7 @@ SIGNATURES = {
     "scan_batch_size": (_I32, [_VP]),
     "scan_batch_union": (_VP, [_VP]),
     "scan_batch_query": (ctypes.c_int, [_VP, _VP, _U32, _VP]),
+    "scan_batch_query_packed": (ctypes.c_int, [_VP, _VP, _U32, _PP, _VP, _VP]),
     "scan_batch_query_device": (ctypes.c_int, [_VP, _VP, _U32, ctypes.POINTER(scan_device_out)]),
     "scan_batch_free": (None, [_VP]),
     "scan_query_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
@@ -408,6 +409,22 @@ def scan_batch_query(b: int, params, mode: int = SCAN_Q_RECOMPUTE) -> list:
     outs = (ctypes.c_void_p * k)()
     _check(lib().scan_batch_query(b, _params_array(params), mode, outs))
     return [_result_to_numpy(outs[j]) for j in range(k)]
+
+
+def scan_batch_query_packed(b: int, params, mode: int = SCAN_Q_RECOMPUTE) -> list:
+    """The same answers as scan_batch_query from one packed result: each
+    graph's dict holds numpy views into the one result's arrays."""
+    k = scan_batch_size(b)
+    assert len(params) == k
+    out = ctypes.c_void_p()
+    voff = np.zeros(k + 1, np.int64)
+    poff = np.zeros(k + 1, np.int64)
+    _check(lib().scan_batch_query_packed(b, _params_array(params), mode, ctypes.byref(out), voff.ctypes.data,
+                                         poff.ctypes.data))
+    whole = _result_to_numpy(out.value)
+    core, cid, label, pairs = whole["core"], whole["cid"], whole["label"], whole["pairs"]
+    return [{"core": core[voff[j]:voff[j + 1]], "cid": cid[voff[j]:voff[j + 1]],
+             "label": label[voff[j]:voff[j + 1]], "pairs": pairs[poff[j]:poff[j + 1]]} for j in range(k)]
 
 
 def scan_batch_query_device(b: int, params, mode: int, core: int, cid: int, label: int, pairs: int,

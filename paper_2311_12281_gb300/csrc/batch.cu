@@ -466,6 +466,82 @@ scan_status scan_batch_query(scan_batch *b, const scan_params *params, uint32_t 
     }
 }
 
+scan_status scan_batch_query_packed(scan_batch *b, const scan_params *params, uint32_t mode, scan_result **out,
+                                    int64_t *vertex_offsets, int64_t *pair_offsets) {
+    try {
+        if (!b || !params || !out || !vertex_offsets || !pair_offsets) {
+            set_error("NULL argument");
+            return SCAN_EINVAL;
+        }
+        *out = nullptr;
+        Ctx *c = b->ctx;
+        Graph *g = b->g;
+        SCAN_CUDA(cudaSetDevice(c->device));
+        SCAN_TRY(batch_query_to_device(b, params, mode, (uint8_t *)g->core.ptr, (int32_t *)g->cid.ptr,
+                                       (uint8_t *)g->label.ptr, (int32_t *)g->pairs.ptr, g->nnz,
+                                       (int64_t *)g->npairs.ptr));
+        SCAN_CUDA(cudaMemcpyAsync(g->h_npairs, g->npairs.ptr, 8, cudaMemcpyDeviceToHost, c->stream));
+        SCAN_TRY(take_device_error(g));
+        const int64_t kp = *g->h_npairs, n = g->n;
+        // the union's arrays straight into one pinned result
+        scan_result *r = result_new(g->n, kp, true);
+        if (!r) {
+            set_error("pinned result allocation failed");
+            return SCAN_ENOMEM;
+        }
+        cudaError_t e = cudaSuccess;
+        if (n > 0) {
+            e = cudaMemcpyAsync(r->core, g->core.ptr, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->cid, g->cid.ptr, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->label, g->label.ptr, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess && kp > 0)
+            e = cudaMemcpyAsync(r->pairs, g->pairs.ptr, 8 * (size_t)kp, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            scan_result_free(r);
+            return cuda_fail(e, "batch result download");
+        }
+        // pairs are sorted by union vertex, so each graph owns a contiguous run
+        const int32_t k = b->k;
+        for (int32_t j = 0; j <= k; ++j) {
+            const int64_t vb = j < k ? b->vbase[j] : n;
+            int64_t lo = 0, hi = kp;  // first pair whose vertex is >= vb
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (r->pairs[2 * mid] < vb) lo = mid + 1;
+                else hi = mid;
+            }
+            pair_offsets[j] = lo;
+            vertex_offsets[j] = vb;
+        }
+        // union ids to each graph's own ids, the graphs shared out over a few host threads
+        auto local = [&](int32_t j0, int32_t j1) {
+            for (int32_t j = j0; j < j1; ++j) {
+                const int32_t vb = (int32_t)b->vbase[j], ve = (int32_t)b->vbase[j + 1];
+                for (int32_t v = vb; v < ve; ++v)
+                    if (r->cid[v] >= 0) r->cid[v] -= vb;
+                for (int64_t i = pair_offsets[j]; i < pair_offsets[j + 1]; ++i) {
+                    r->pairs[2 * i] -= vb;
+                    r->pairs[2 * i + 1] -= vb;
+                }
+            }
+        };
+        const int32_t nt = (int32_t)std::min<int64_t>({8, std::max(1u, std::thread::hardware_concurrency()), k});
+        std::vector<std::thread> pool;
+        for (int32_t t = 1; t < nt; ++t)
+            pool.emplace_back(local, (int32_t)((int64_t)k * t / nt), (int32_t)((int64_t)k * (t + 1) / nt));
+        local(0, (int32_t)((int64_t)k / nt));
+        for (auto &th : pool) th.join();
+        *out = r;
+        return SCAN_OK;
+    } catch (...) {
+        set_error("host allocation failed");
+        return SCAN_ENOMEM;
+    }
+}
+
 scan_status scan_query_batch(scan_graph *const *gs, const scan_params *params, int32_t k, scan_result **outs) {
     try {
         if (!gs || !params || !outs || k < 1 || !gs[0]) { set_error("bad arguments"); return SCAN_EINVAL; }

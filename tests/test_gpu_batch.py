@@ -156,3 +156,27 @@ def test_replayed_batch_queries_follow_new_parameters(ps, ctx):
                 base += g.n
     finally:
         ps.scan_batch_free(b)
+
+
+@pytest.mark.parametrize("mode", ["recompute", "cache"])
+def test_packed_batch_result_equals_per_graph_results_and_oracle(ps, ctx, mode):
+    # one result over the whole batch: each member's ranges hold its own ids
+    graphs, params = small_batch(40, seed=6100)
+    b = ps.scan_batch_load(ctx.handle, graphs)
+    try:
+        m = ps.SCAN_Q_RECOMPUTE if mode == "recompute" else ps.SCAN_Q_BUILD_CACHE
+        packed = ps.scan_batch_query_packed(b, params, m)
+        per = ps.scan_batch_query(b, params, ps.SCAN_Q_AUTO if mode == "cache" else m)
+        assert len(packed) == len(per) == len(graphs)
+        for j, (g, (p, q, mu)) in enumerate(zip(graphs, params)):
+            assert packed[j]["core"].shape == (g.n,)
+            assert_same(packed[j], per[j], f"packed vs per-graph member {j}")
+            assert_same(packed[j], oracle.scan(g, p, q, mu), f"packed member {j} eps={p}/{q} mu={mu}")
+        # the views outlive the batch
+        keep = packed[3]
+        ps.scan_batch_free(b)
+        b = None
+        assert_same(keep, oracle.scan(graphs[3], *params[3]), "kept view")
+    finally:
+        if b is not None:
+            ps.scan_batch_free(b)
