@@ -679,7 +679,8 @@ def run_plan(args):
     """Transfer volume of one out-of-core query under a device budget: the
     row-block pairs this library streams (measured: the host-to-device bytes
     of one query), against the paper's edge extended subgraphs (Algorithm 5,
-    planned on the host: each subgraph loaded once, Memof = 25|E| + 4|V|)."""
+    planned on the host: each subgraph loaded once, Memof = 25|E| + 4|V|) and
+    the host plan of triangle counting over rank-ordered block pairs."""
     import paper_2311_12281_gb300 as ps
     from paper_2311_12281_gb300 import _build
 
@@ -698,6 +699,7 @@ def run_plan(args):
     t = time.perf_counter()
     k, plan_bytes = ps.scan_plan_edge_extended(g.n, g.offsets, g.adj, budget)
     plan_s = time.perf_counter() - t
+    tb, tpairs, tri_bytes = ps.scan_plan_triangle_blocks(g.n, g.offsets, g.adj, budget)
     csr = g.offsets.nbytes + g.adj.nbytes
     line = {"metric": "out-of-core transfer bytes per query", "unit": "bytes", "higher_is_better": False,
             "value": row_bytes, "n_gpus": 1, "data": "synthetic", "dtype": "i32", "vs_baseline": None,
@@ -708,7 +710,11 @@ def run_plan(args):
             "edge_extended_subgraphs": {"subgraphs": k, "bytes_per_query": plan_bytes, "x_csr": plan_bytes / csr,
                                         "planning_s_host": plan_s,
                                         "what": "the paper's Algorithm 5 partition (host plan): each subgraph "
-                                                "loaded once, Memof = 25|E_s| + 4|V_s|"}}
+                                                "loaded once, Memof = 25|E_s| + 4|V_s|"},
+            "triangle_block_pairs": {"blocks": tb, "pairs": tpairs, "bytes_per_query": tri_bytes,
+                                     "x_csr": tri_bytes / csr,
+                                     "what": "host plan of triangle counting over rank-ordered block pairs "
+                                             "(out-lists and counts streamed; not yet a driver)"}}
     print(json.dumps(line), flush=True)
 
 

@@ -188,6 +188,26 @@ SCAN_API scan_status scan_graph_set_zero_copy(scan_graph *g, int32_t enable);
  */
 SCAN_API scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
                                              uint64_t device_bytes, int64_t *subgraphs, uint64_t *bytes);
+/*
+ * Plan (host only, no device work) of counting by degree-oriented triangle
+ * enumeration (Section 4.1's orientation) over pairs of vertex blocks, for a
+ * graph whose CSR stays in host memory. A triangle a < b < c in (deg, id)
+ * rank is found at b, and its three counts lie in out(a) and out(b), so the
+ * pair (block of a, block of b) needs only those two blocks; blocks are cut
+ * in rank order, so only pairs i <= j carry work. The device keeps 19 B per
+ * vertex and a bit per slot; three block slots share 90 % of the rest, a
+ * block holding whole out-lists at 8 B per oriented edge and 12 B per row.
+ * Returns the blocks, the pairs with at least one oriented edge from block i
+ * to block j, and the bytes moved when each block is loaded (12 B per row
+ * and 8 B per oriented edge in) and unloaded (4 B per oriented edge out) once
+ * as the resident block and once per later pair that streams it.
+ * SCAN_EINVAL on malformed offsets or ids out of range; SCAN_EBUDGET when
+ * device_bytes cannot hold the per-vertex state or one out-list, or would
+ * need more than 8192 blocks.
+ */
+SCAN_API scan_status scan_plan_triangle_blocks(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                                               uint64_t device_bytes, int32_t *blocks, int64_t *pairs,
+                                               uint64_t *bytes);
 SCAN_API int32_t scan_graph_n(const scan_graph *g);
 SCAN_API int64_t scan_graph_nnz(const scan_graph *g);
 /* Device bytes held by this graph (including its count cache). */

@@ -84,6 +84,8 @@ SIGNATURES = {
     "scan_graph_set_zero_copy": (ctypes.c_int, [_VP, _I32]),
     "scan_plan_edge_extended": (ctypes.c_int, [_I32, _VP, _VP, _I64, _U64, ctypes.POINTER(ctypes.c_int64),
                                                ctypes.POINTER(ctypes.c_uint64)]),
+    "scan_plan_triangle_blocks": (ctypes.c_int, [_I32, _VP, _VP, _I64, _U64, ctypes.POINTER(ctypes.c_int32),
+                                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64)]),
     "scan_graph_n": (_I32, [_VP]),
     "scan_graph_nnz": (_I64, [_VP]),
     "scan_graph_device_bytes": (_U64, [_VP]),
@@ -250,6 +252,18 @@ def scan_plan_edge_extended(n: int, offsets: np.ndarray, adj: np.ndarray, device
     _check(lib().scan_plan_edge_extended(int(n), off.ctypes.data, a.ctypes.data if a.size else None, int(a.size),
                                          int(device_bytes), ctypes.byref(k), ctypes.byref(b)))
     return k.value, b.value
+
+
+def scan_plan_triangle_blocks(n: int, offsets: np.ndarray, adj: np.ndarray, device_bytes: int) -> tuple[int, int, int]:
+    """(blocks, pairs with work, bytes) of triangle counting over block pairs out of core (host only)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    a = np.ascontiguousarray(adj, dtype=np.int32)
+    nb = ctypes.c_int32()
+    npairs = ctypes.c_int64()
+    b = ctypes.c_uint64()
+    _check(lib().scan_plan_triangle_blocks(int(n), off.ctypes.data, a.ctypes.data if a.size else None, int(a.size),
+                                           int(device_bytes), ctypes.byref(nb), ctypes.byref(npairs), ctypes.byref(b)))
+    return nb.value, npairs.value, b.value
 
 
 def scan_graph_n(g: int) -> int:

@@ -427,10 +427,9 @@ int32_t scan_graph_blocks(const scan_graph *g) {
 
 uint64_t scan_graph_transfer_bytes(const scan_graph *g) { return g && g->part ? part_transfer_bytes(g) : 0; }
 
-scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
-                                    uint64_t device_bytes, int64_t *subgraphs, uint64_t *bytes) {
-    ABI_GUARD_BEGIN
-    if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj) || !subgraphs || !bytes) {
+// The checks of a host CSR that the planners need: sizes, offsets, ids in range.
+static scan_status check_host_csr(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz) {
+    if (n < 0 || nnz < 0 || (n > 0 && !offsets) || (nnz > 0 && !adj)) {
         set_error("bad sizes or NULL arrays");
         return SCAN_EINVAL;
     }
@@ -448,7 +447,30 @@ scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int
             set_error("id out of range at slot " + std::to_string(s));
             return SCAN_EINVAL;
         }
+    return SCAN_OK;
+}
+
+scan_status scan_plan_edge_extended(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                                    uint64_t device_bytes, int64_t *subgraphs, uint64_t *bytes) {
+    ABI_GUARD_BEGIN
+    if (!subgraphs || !bytes) {
+        set_error("NULL output");
+        return SCAN_EINVAL;
+    }
+    SCAN_TRY(check_host_csr(n, offsets, adj, nnz));
     return plan_edge_extended(n, offsets, adj, nnz, device_bytes, subgraphs, bytes);
+    ABI_GUARD_END
+}
+
+scan_status scan_plan_triangle_blocks(int32_t n, const int64_t *offsets, const int32_t *adj, int64_t nnz,
+                                      uint64_t device_bytes, int32_t *blocks, int64_t *pairs, uint64_t *bytes) {
+    ABI_GUARD_BEGIN
+    if (!blocks || !pairs || !bytes) {
+        set_error("NULL output");
+        return SCAN_EINVAL;
+    }
+    SCAN_TRY(check_host_csr(n, offsets, adj, nnz));
+    return plan_triangle_blocks(n, offsets, adj, nnz, device_bytes, blocks, pairs, bytes);
     ABI_GUARD_END
 }
 

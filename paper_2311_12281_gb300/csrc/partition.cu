@@ -496,6 +496,99 @@ scan_status plan_edge_extended(int32_t n, const int64_t *off, const int32_t *adj
     return SCAN_OK;
 }
 
+// Plan of triangle enumeration over block pairs out of core (host only).
+// For a triangle a < b < c in (deg, id) rank, found at its middle vertex b,
+// the three counts lie in out(a) and out(b) (Section 4.1's degree-oriented
+// lists), so the pair (block of a, block of b) needs only those two blocks'
+// out-lists and counts; with blocks cut in rank order a < b puts block(a) <=
+// block(b). The device keeps the per-vertex state (19 B per vertex, as the
+// row-block driver) and one similarity bit per slot; three block slots (the
+// resident block, the streamed one and its prefetch) share 90 % of the rest.
+// A block holds whole out-lists: 8 B per oriented edge (id, count) and 12 B
+// per row. The bytes are those of each block loaded (ids and counts in) and
+// unloaded (counts out) once as the resident block and once for every later
+// pair (i < j) that holds an oriented edge from block i to block j.
+scan_status plan_triangle_blocks(int32_t n, const int64_t *off, const int32_t *adj, int64_t nnz, uint64_t mem,
+                                 int32_t *blocks, int64_t *pairs, uint64_t *bytes) {
+    *blocks = 0;
+    *pairs = 0;
+    *bytes = 0;
+    if (n == 0) return SCAN_OK;
+    const uint64_t state = 19ull * ((uint64_t)n + 1) + (uint64_t)nnz / 8 + 16;
+    if (mem <= state) {
+        set_error("device_bytes does not hold the per-vertex state");
+        return SCAN_EBUDGET;
+    }
+    const double cap = 0.9 * (double)(mem - state) / 3.0;
+    // rank order (deg, id): a counting sort by degree keeps ids ascending within a degree
+    std::vector<int64_t> start((size_t)n + 2, 0);
+    // degrees are at most n - 1 in a simple graph; larger ones share the last bucket
+    for (int32_t v = 0; v < n; ++v) ++start[(size_t)std::min<int64_t>(off[v + 1] - off[v], n) + 1];
+    for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
+    std::vector<int32_t> order((size_t)n);
+    {
+        std::vector<int64_t> cur(start.begin(), start.end() - 1);
+        for (int32_t v = 0; v < n; ++v) {
+            const size_t d = (size_t)std::min<int64_t>(off[v + 1] - off[v], n);
+            order[(size_t)cur[d]++] = v;
+        }
+    }
+    auto above = [&](int32_t x, int32_t y) {  // y ranks above x
+        const int64_t dx = off[x + 1] - off[x], dy = off[y + 1] - off[y];
+        return dy > dx || (dy == dx && y > x);
+    };
+    std::vector<int32_t> blk((size_t)n, 0);
+    std::vector<int64_t> bedges, brows;
+    double used = 0;
+    int64_t e_cur = 0, r_cur = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t v = order[(size_t)i];
+        int64_t dp = 0;
+        for (int64_t s = off[v]; s < off[v + 1]; ++s) dp += above(v, adj[s]) ? 1 : 0;
+        const double row = 12.0 + 8.0 * (double)dp;
+        if (row > cap) {
+            set_error("an out-list of " + std::to_string(dp) + " ids does not fit a block slot");
+            return SCAN_EBUDGET;
+        }
+        if (used + row > cap && r_cur > 0) {
+            bedges.push_back(e_cur);
+            brows.push_back(r_cur);
+            used = 0;
+            e_cur = r_cur = 0;
+        }
+        blk[(size_t)v] = (int32_t)bedges.size();
+        used += row;
+        e_cur += dp;
+        ++r_cur;
+    }
+    bedges.push_back(e_cur);
+    brows.push_back(r_cur);
+    const int64_t P = (int64_t)bedges.size();
+    if (P > 8192) {
+        set_error("more than 8192 blocks: device_bytes is too small for this graph");
+        return SCAN_EBUDGET;
+    }
+    std::vector<uint8_t> work((size_t)(P * P), 0);
+    for (int32_t a = 0; a < n; ++a)
+        for (int64_t s = off[a]; s < off[a + 1]; ++s)
+            if (above(a, adj[s])) work[(size_t)(blk[(size_t)a] * P + blk[(size_t)adj[s]])] = 1;
+    auto moved = [&](int64_t j) { return 12ull * (uint64_t)brows[(size_t)j] + 12ull * (uint64_t)bedges[(size_t)j]; };
+    uint64_t total = 0;
+    int64_t np = 0;
+    for (int64_t i = 0; i < P; ++i) {
+        total += moved(i);
+        for (int64_t j = i; j < P; ++j) {
+            if (!work[(size_t)(i * P + j)]) continue;
+            ++np;
+            if (j > i) total += moved(j);
+        }
+    }
+    *blocks = (int32_t)P;
+    *pairs = np;
+    *bytes = total;
+    return SCAN_OK;
+}
+
 scan_status part_set_zero_copy(Graph *g, bool on) {
     Part *P = g->part;
     Ctx *c = g->ctx;

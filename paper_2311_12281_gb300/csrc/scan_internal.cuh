@@ -254,6 +254,8 @@ uint64_t part_transfer_bytes(const Graph *g);
 scan_status part_set_zero_copy(Graph *g, bool on);
 scan_status plan_edge_extended(int32_t n, const int64_t *off, const int32_t *adj, int64_t nnz, uint64_t mem,
                                int64_t *subgraphs, uint64_t *bytes);
+scan_status plan_triangle_blocks(int32_t n, const int64_t *off, const int32_t *adj, int64_t nnz, uint64_t mem,
+                                 int32_t *blocks, int64_t *pairs, uint64_t *bytes);
 
 #define SCAN_CUDA(call)                                              \
     do {                                                             \
